@@ -1,0 +1,537 @@
+"""Plain, slow FP64 CPU oracle for GLS estimation of SUR models by PCG-Aug.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this
+module: only the test-suite, the package's smoke check and the benchmark's
+CPU-baseline leg use it.  It shares no code with the CUDA library; its inputs
+come from the seeded generators in ``synth.sur_inputs``.
+
+Everything here is float64 numpy, written for a reader to check against the
+paper (Foschi, "Preconditioned Conjugate Gradient methods for the estimation
+of General Linear Models"):
+
+  * ``aug_dense_solve``   -- brute force: the augmented system eq. (aug1)
+                             built densely and solved (min-norm LS if singular).
+  * ``gls_formula``       -- eq. (GLS), b = (X^T S^-1 X)^-1 X^T S^-1 y (PD only).
+  * ``aug_lemma``         -- Lemma thm:AugBLUE closed form (eq. augsol).
+  * ``ols_blocks``        -- per-block OLS of the SUR model (Sec. 1).
+  * ``sur_gls_structured``-- structured direct GLS: Remark rem:reduction, then
+                             an eigen-split of Omega; zero-variance directions
+                             become exact restrictions (Sec. 5.1 idea).
+  * ``pcg``               -- Algorithm pcg on dense (G, K, h).
+  * ``sur_pcg_aug``       -- Algorithm glmpcg2 (PCG-Aug) with D = I in the SUR
+                             form of Sec. 5.3 (per-block QR, Sigma u = vec(U Omega)).
+  * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
+                             Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
+  * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
+
+Layouts: X_blocks list of (M, n_i); Omega (G, G); Y (m, k) with column j =
+vec(Y_j) (block i occupies rows i*M .. (i+1)*M); b (n, k).
+
+Parity status: every function above is pinned by tests/test_oracle_pins.py
+against brute force, closed forms, invariants or textbook special cases.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "sur_dense", "augmented_matrix", "aug_dense_solve", "gls_formula", "aug_lemma",
+    "ols_blocks", "sur_gls_structured", "pcg", "sur_pcg_aug", "rglm_pcg_aug",
+    "sur_gls_gradient", "augmented_residual", "lse_solve",
+]
+
+
+# ----------------------------------------------------------------------------
+# dense building blocks (Sec. 1 SUR structure; eq. aug1)
+# ----------------------------------------------------------------------------
+
+def sur_dense(X_blocks, Omega):
+    """Dense Sigma = Omega (x) I_M and X = (+)_i X_i (Sec. 1)."""
+    M = X_blocks[0].shape[0]
+    Sigma = np.kron(Omega, np.eye(M))
+    n = sum(x.shape[1] for x in X_blocks)
+    X = np.zeros((len(X_blocks) * M, n))
+    off = 0
+    for i, Xi in enumerate(X_blocks):
+        X[i * M:(i + 1) * M, off:off + Xi.shape[1]] = Xi
+        off += Xi.shape[1]
+    return Sigma, X
+
+
+def augmented_matrix(Sigma, X):
+    """[[Sigma, X], [X^T, 0]] of eq. (aug1)."""
+    m, n = X.shape
+    K = np.zeros((m + n, m + n))
+    K[:m, :m] = Sigma
+    K[:m, m:] = X
+    K[m:, :m] = X.T
+    return K
+
+
+def _pinv_solve(K, H):
+    """Minimum-norm least-squares solution of K x = H via the SVD (handles a
+    singular augmented matrix; the b-part of any solution is unique when X
+    has full column rank)."""
+    U, s, Vt = np.linalg.svd(K)
+    r = int(np.sum(s > s[0] * max(K.shape) * np.finfo(float).eps))
+    return Vt[:r].T @ ((U[:, :r].T @ H) / s[:r, None])
+
+
+def aug_dense_solve(X_blocks, Omega, Y, C=None, d=None):
+    """Brute force (O1): build eq. (aug1) densely and solve it.
+
+    With restrictions C b = d the model is the GLM of eq. (RGLM1setup):
+    Sigma_aug = diag(Sigma, 0), X_aug = [X; C], y_aug = [y; d].
+    Returns (w, b): w of length m (+ kc), b (n, k)."""
+    Sigma, X = sur_dense(X_blocks, Omega)
+    Y = np.asarray(Y, dtype=float).reshape(Sigma.shape[0], -1)
+    if C is not None:
+        kc = C.shape[0]
+        m = Sigma.shape[0]
+        S2 = np.zeros((m + kc, m + kc))
+        S2[:m, :m] = Sigma
+        Sigma = S2
+        X = np.vstack([X, C])
+        Y = np.vstack([Y, np.asarray(d, dtype=float).reshape(kc, -1)])
+    m, n = X.shape
+    K = augmented_matrix(Sigma, X)
+    H = np.vstack([Y, np.zeros((n, Y.shape[1]))])
+    try:
+        x = np.linalg.solve(K, H)
+        if not np.all(np.isfinite(x)) or np.linalg.cond(K) > 1e14:
+            raise np.linalg.LinAlgError
+    except np.linalg.LinAlgError:
+        x = _pinv_solve(K, H)
+    return x[:m], x[m:]
+
+
+def gls_formula(X_blocks, Omega, Y):
+    """eq. (GLS): b = (X^T Sigma^-1 X)^-1 X^T Sigma^-1 y with
+    Sigma^-1 = Omega^-1 (x) I_M (Omega positive definite only)."""
+    M = X_blocks[0].shape[0]
+    _, X = sur_dense(X_blocks, Omega)
+    Si = np.kron(np.linalg.inv(Omega), np.eye(M))
+    A = X.T @ Si @ X
+    return np.linalg.solve(A, X.T @ Si @ np.asarray(Y).reshape(X.shape[0], -1))
+
+
+def aug_lemma(X_blocks, Omega, Y):
+    """Lemma thm:AugBLUE (eq. augsol): with the full QR X = [Q_R Q_N][R; 0],
+    w = Q_N (Q_N^T Sigma Q_N)^-1 Q_N^T y,
+    b = R^-1 Q_R^T P_N y,  P_N = I - Sigma Q_N (Q_N^T Sigma Q_N)^-1 Q_N^T."""
+    Sigma, X = sur_dense(X_blocks, Omega)
+    m, n = X.shape
+    Y = np.asarray(Y).reshape(m, -1)
+    Qf, Rf = np.linalg.qr(X, mode="complete")
+    QR_, QN = Qf[:, :n], Qf[:, n:]
+    R = Rf[:n]
+    A = QN.T @ Sigma @ QN
+    w = QN @ np.linalg.solve(A, QN.T @ Y)
+    PN_y = Y - Sigma @ QN @ np.linalg.solve(A, QN.T @ Y)
+    b = np.linalg.solve(R, QR_.T @ PN_y)
+    return w, b
+
+
+def ols_blocks(X_blocks, Y):
+    """Per-block OLS of the SUR model (Sec. 1): b_i = (X_i^T X_i)^-1 X_i^T y_i."""
+    M = X_blocks[0].shape[0]
+    Y = np.asarray(Y).reshape(len(X_blocks) * M, -1)
+    out = []
+    for i, Xi in enumerate(X_blocks):
+        out.append(np.linalg.solve(Xi.T @ Xi, Xi.T @ Y[i * M:(i + 1) * M]))
+    return np.vstack(out)
+
+
+# ----------------------------------------------------------------------------
+# structured direct GLS (Remark rem:reduction + eigen-split of Omega)
+# ----------------------------------------------------------------------------
+
+def lse_solve(A, a, B=None, bc=None):
+    """min ||A x - a|| subject to B x = bc (B consistent, may be tall or
+    rank deficient), by the null-space method with an SVD of B."""
+    if B is None or B.shape[0] == 0:
+        return np.linalg.lstsq(A, a, rcond=None)[0]
+    U, s, Vt = np.linalg.svd(B, full_matrices=True)
+    r = int(np.sum(s > s[0] * max(B.shape) * np.finfo(float).eps * 16))
+    xp = Vt[:r].T @ ((U[:, :r].T @ bc) / s[:r, None])
+    N = Vt[r:].T
+    if N.shape[1] == 0 or A.shape[0] == 0:
+        return xp
+    t = np.linalg.lstsq(A @ N, a - A @ xp, rcond=None)[0]
+    return xp + N @ t
+
+
+def range_basis(W):
+    """Orthonormal basis of range(W): thin Householder QR when W is tall with
+    full column rank, otherwise the left singular vectors above a threshold."""
+    M, n = W.shape
+    if M >= n:
+        Qw, Rw = np.linalg.qr(W)
+        dg = np.abs(np.diag(Rw))
+        if dg.min() > 1e-10 * dg.max():
+            return Qw
+    U, s, _ = np.linalg.svd(W, full_matrices=False)
+    r = int(np.sum(s > s[0] * max(W.shape) * np.finfo(float).eps))
+    return U[:, :r]
+
+
+def sur_gls_structured(X_blocks, Omega, Y, C=None, d=None, tau_rel=None):
+    """Structured direct GLS (O2).
+
+    1. Remark rem:reduction: with B an orthonormal basis of range(W),
+       W = [X_1 ... X_G], replace y_i, X_i by B^T y_i, B^T X_i (q rows each).
+       Rows orthogonal to range(W) carry no regressor and, as Sigma = Omega (x) I
+       keeps rows independent, no information on beta.
+    2. Omega = V diag(lam) V^T.  Right-multiplying the reduced M x G model by
+       V decouples it into G independent regressions: equation j has
+       regressor [v_1j X_1, ..., v_Gj X_G] and disturbance variance lam_j.
+    3. lam_j > tau: weighted LS rows (scaled by lam_j^-1/2);  lam_j <= tau:
+       exact (zero-variance) restrictions, as in eq. (RGLM1setup).
+       Rows [C | d] are appended as restrictions.
+    4. Solve the equality-constrained LS problem (``lse_solve``).
+    tau = tau_rel * lam_max with tau_rel = sqrt(eps) by default."""
+    G = len(X_blocks)
+    M = X_blocks[0].shape[0]
+    n_i = [x.shape[1] for x in X_blocks]
+    n = sum(n_i)
+    Y = np.asarray(Y, dtype=float).reshape(G * M, -1)
+    k = Y.shape[1]
+    Bw = range_basis(np.hstack(X_blocks))
+    Xr = [Bw.T @ Xi for Xi in X_blocks]                       # q x n_i
+    lam, V = np.linalg.eigh(0.5 * (Omega + Omega.T))
+    if tau_rel is None:
+        tau_rel = np.sqrt(np.finfo(float).eps)
+    tau = tau_rel * max(lam.max(), 0.0)
+    offs = np.cumsum([0] + n_i)
+    ls_A, con_A, ls_j, con_j = [], [], [], []
+    for j in range(G):
+        Aj = np.zeros((Bw.shape[1], n))
+        for i in range(G):
+            Aj[:, offs[i]:offs[i + 1]] = V[i, j] * Xr[i]
+        if lam[j] > tau:
+            ls_A.append(Aj / np.sqrt(lam[j]))
+            ls_j.append(j)
+        else:
+            con_A.append(Aj)
+            con_j.append(j)
+    A = np.vstack(ls_A) if ls_A else np.zeros((0, n))
+    Bc = np.vstack(con_A) if con_A else np.zeros((0, n))
+    if C is not None:
+        Bc = np.vstack([Bc, C])
+    out = np.empty((n, k))
+    for c in range(k):
+        Yr = Bw.T @ Y[:, c].reshape(G, M).T                   # q x G reduced responses
+        Yt = Yr @ V                                           # decoupled responses
+        a = np.concatenate([Yt[:, j] / np.sqrt(lam[j]) for j in ls_j]) if ls_j else np.zeros(0)
+        bc = np.concatenate([Yt[:, j] for j in con_j]) if con_j else np.zeros(0)
+        if C is not None:
+            bc = np.concatenate([bc, np.asarray(d, dtype=float).reshape(C.shape[0], -1)[:, c]])
+        out[:, c] = lse_solve(A, a[:, None], Bc if Bc.shape[0] else None,
+                              bc[:, None] if Bc.shape[0] else None)[:, 0]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# PCG (Algorithm pcg) and PCG-Aug (Algorithm glmpcg2) in the SUR form
+# ----------------------------------------------------------------------------
+
+def pcg(Gm, Km, h, x1, iters):
+    """Algorithm pcg, verbatim in the paper's notation, for ``iters`` steps on
+    dense symmetric G and K; residual convention f = G x - h.  Returns the list
+    of iterates x_1 .. x_{iters+1} (stops early if d_i == 0)."""
+    x = x1.copy()
+    f = Gm @ x - h
+    p = Km @ f
+    c = f @ (Km @ f)
+    xs = [x.copy()]
+    for _ in range(iters):
+        Gp = Gm @ p
+        dd = p @ Gp
+        if dd == 0.0:
+            break
+        lam = c / dd
+        x = x - lam * p
+        f = f - lam * Gp
+        Kf = Km @ f
+        c_new = f @ Kf
+        mu = c_new / c
+        p = Kf + mu * p
+        c = c_new
+        xs.append(x.copy())
+    return xs
+
+
+class SurOps:
+    """The SUR applies of Sec. 5.3 with D = I, from thin QRs X_i = Q_i R_i:
+      Pi xi      = vec(xi_i - Q_i Q_i^T xi_i)
+      X*^T xi    = vec(R_i^-1 Q_i^T xi_i)
+      X v        = vec(X_i v_i)
+      Sigma u    = vec(U Omega),  u = vec(U)."""
+
+    def __init__(self, X_blocks, Omega):
+        self.X = X_blocks
+        self.Omega = np.asarray(Omega, dtype=float)
+        self.G = len(X_blocks)
+        self.M = X_blocks[0].shape[0]
+        self.n_i = [x.shape[1] for x in X_blocks]
+        self.offs = np.cumsum([0] + self.n_i)
+        self.QR = [np.linalg.qr(Xi) for Xi in X_blocks]
+
+    def sigma(self, u):
+        k = u.shape[1]
+        U = u.reshape(self.G, self.M, k)                      # U[i] = column i of each U_j
+        S = np.einsum("gh,gmk->hmk", self.Omega, U)           # (U Omega)_h = sum_g U_g w_gh
+        return S.reshape(self.G * self.M, k)
+
+    def pi(self, xi):
+        out = np.empty_like(xi)
+        M = self.M
+        for i, (Qi, _) in enumerate(self.QR):
+            blk = xi[i * M:(i + 1) * M]
+            out[i * M:(i + 1) * M] = blk - Qi @ (Qi.T @ blk)
+        return out
+
+    def xstar_t(self, xi):
+        M = self.M
+        parts = []
+        for i, (Qi, Ri) in enumerate(self.QR):
+            parts.append(np.linalg.solve(Ri, Qi.T @ xi[i * M:(i + 1) * M]))
+        return np.vstack(parts)
+
+    def xmul(self, v):
+        M = self.M
+        out = np.empty((self.G * M, v.shape[1]))
+        for i, Xi in enumerate(self.X):
+            out[i * M:(i + 1) * M] = Xi @ v[self.offs[i]:self.offs[i + 1]]
+        return out
+
+    def xt(self, w):
+        M = self.M
+        return np.vstack([Xi.T @ w[i * M:(i + 1) * M] for i, Xi in enumerate(self.X)])
+
+
+STATUS_CONVERGED = "converged"
+STATUS_BREAKDOWN = "breakdown"
+STATUS_STAGNATED = "stagnated"
+STATUS_NOT_CONVERGED = "not_converged"
+
+
+def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=10,
+                record=False, ops=None, w1=None):
+    """Algorithm glmpcg2 (PCG-Aug) with D = I in the SUR form of Sec. 5.3 (O3).
+
+    One independent PCG per column of Y (each with its own c, d, lambda, mu).
+    Start: w_1 = 0 (or ``w1`` with X^T w_1 = 0), z_1 = 0.
+    With D = I, Pi is symmetric and idempotent, so c = r^T Pi r is evaluated
+    as (Pi r)^T (Pi r): the same quantity, without the cancellation of the
+    large range-space part of r against Pi r (which floors sqrt(c/c_1) near
+    sqrt(eps) when written as r . (Pi r)).
+    Stop a column when sqrt(c_{i+1}/c_1) <= tol (converged), when d_i <= 0 or
+    is not finite (breakdown), when c_{i+1} >= c_{i+1-W} over a window of W
+    steps (stagnation), or at ``maxit``.  Always return
+    z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
+    Returns dict(b, w, iters, status, relres[, history])."""
+    op = ops if ops is not None else SurOps(X_blocks, Omega)
+    m = op.G * op.M
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    k = Y.shape[1]
+    n = int(op.offs[-1])
+    if maxit is None:
+        maxit = m - n + 1
+    w = np.zeros((m, k)) if w1 is None else np.array(w1, dtype=float).reshape(m, k)
+    z = np.zeros((n, k))
+    r = op.sigma(w) + op.xmul(z) - Y                          # step 2
+    Pr = op.pi(r)
+    c = np.sum(Pr * Pr, axis=0)                               # r^T Pi r, Pi = Pi^T Pi
+    u = Pr.copy()                                             # step 3
+    v = op.xstar_t(r)
+    c1 = c.copy()
+    active = c1 > 0
+    iters = np.zeros(k, dtype=int)
+    status = np.array([STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active],
+                      dtype=object)
+    relres = np.where(c1 > 0, 1.0, 0.0)
+    chist = [c.copy()]
+    hist = {"w": [w.copy()], "r": [r.copy()], "u": [u.copy()], "c": [c.copy()]} if record else None
+    for it in range(1, maxit + 1):
+        if not active.any():
+            break
+        Su = op.sigma(u)
+        dd = np.sum(u * Su, axis=0)                           # step 5
+        bad = active & (~np.isfinite(dd) | (dd <= 0))
+        for j in np.where(bad)[0]:
+            status[j] = STATUS_BREAKDOWN
+        active &= ~bad
+        lam = np.where(active, c / np.where(active, dd, 1.0), 0.0)
+        w = w - lam * u                                       # step 6
+        r = r - lam * (Su + op.xmul(v))                       # step 7
+        Pr = op.pi(r)
+        c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)  # step 8
+        iters = iters + active
+        chist.append(c_new.copy())
+        rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
+        relres = np.where(active, rr, relres)
+        conv = active & (rr <= tol)
+        for j in np.where(conv)[0]:
+            status[j] = STATUS_CONVERGED
+        active &= ~conv
+        if it > stag_window:
+            stag = active & (c_new >= chist[-1 - stag_window])
+            for j in np.where(stag)[0]:
+                status[j] = STATUS_STAGNATED
+            active &= ~stag
+        mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
+        v = op.xstar_t(r) + mu * v                            # step 12
+        u = np.where(active, Pr + mu * u, u)
+        c = np.where(active, c_new, c)
+        if record:
+            hist["w"].append(w.copy()); hist["r"].append(r.copy())
+            hist["u"].append(u.copy()); hist["c"].append(c_new.copy())
+    b = op.xstar_t(Y - op.sigma(w))                           # step 10
+    out = dict(b=b, w=w, iters=iters, status=list(status), relres=relres)
+    if record:
+        out["history"] = hist
+    return out
+
+
+def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=10):
+    """Algorithm glmpcg2 on the restricted GLM of Sec. 5.1 with D = I.
+
+    eq. (RGLM1setup): Sigma_aug = diag(Omega (x) I_M, 0_kc), X_aug = [(+)X_i; C],
+    y_aug = [y; d].  eq. (rglm1m) with D_Z = I, D_C = I:
+      X* = X_aug (Z^T Z + C^T C)^-1,   Pi = I - X_aug (Z^T Z + C^T C)^-1 X_aug^T,
+    where Z^T Z = (+)_i X_i^T X_i.  Returns dict(b, w, iters, status, relres)."""
+    G = len(X_blocks)
+    M = X_blocks[0].shape[0]
+    n_i = [x.shape[1] for x in X_blocks]
+    offs = np.cumsum([0] + n_i)
+    n = int(offs[-1])
+    kc = C.shape[0]
+    m = G * M
+    Omega = np.asarray(Omega, dtype=float)
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    k = Y.shape[1]
+    yaug = np.vstack([Y, np.asarray(d, dtype=float).reshape(kc, k)])
+    Nmat = C.T @ C
+    for i, Xi in enumerate(X_blocks):
+        Nmat[offs[i]:offs[i + 1], offs[i]:offs[i + 1]] += Xi.T @ Xi
+
+    def xt(xi):                                               # X_aug^T xi
+        top = np.vstack([X_blocks[i].T @ xi[i * M:(i + 1) * M] for i in range(G)])
+        return top + C.T @ xi[m:]
+
+    def xmul(v):                                              # X_aug v
+        out = np.empty((m + kc, v.shape[1]))
+        for i in range(G):
+            out[i * M:(i + 1) * M] = X_blocks[i] @ v[offs[i]:offs[i + 1]]
+        out[m:] = C @ v
+        return out
+
+    def xstar_t(xi):
+        return np.linalg.solve(Nmat, xt(xi))
+
+    def pi(xi):
+        return xi - xmul(xstar_t(xi))
+
+    def sigma(u):
+        U = u[:m].reshape(G, M, -1)
+        S = np.einsum("gh,gmk->hmk", Omega, U).reshape(m, -1)
+        return np.vstack([S, np.zeros((kc, u.shape[1]))])
+
+    if maxit is None:
+        maxit = m + kc - n + 1
+    w = np.zeros((m + kc, k))
+    r = sigma(w) - yaug
+    Pr = pi(r)
+    c = np.sum(Pr * Pr, axis=0)
+    u = Pr.copy()
+    v = xstar_t(r)
+    c1 = c.copy()
+    active = c1 > 0
+    iters = np.zeros(k, dtype=int)
+    status = [STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active]
+    relres = np.where(c1 > 0, 1.0, 0.0)
+    chist = [c.copy()]
+    for it in range(1, maxit + 1):
+        if not active.any():
+            break
+        Su = sigma(u)
+        dd = np.sum(u * Su, axis=0)
+        bad = active & (~np.isfinite(dd) | (dd <= 0))
+        for j in np.where(bad)[0]:
+            status[j] = STATUS_BREAKDOWN
+        active &= ~bad
+        lam = np.where(active, c / np.where(active, dd, 1.0), 0.0)
+        w = w - lam * u
+        r = r - lam * (Su + xmul(v))
+        Pr = pi(r)
+        c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)
+        iters = iters + active
+        chist.append(c_new.copy())
+        rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
+        relres = np.where(active, rr, relres)
+        conv = active & (rr <= tol)
+        for j in np.where(conv)[0]:
+            status[j] = STATUS_CONVERGED
+        active &= ~conv
+        if it > stag_window:
+            stag = active & (c_new >= chist[-1 - stag_window])
+            for j in np.where(stag)[0]:
+                status[j] = STATUS_STAGNATED
+            active &= ~stag
+        mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
+        v = xstar_t(r) + mu * v
+        u = np.where(active, Pr + mu * u, u)
+        c = np.where(active, c_new, c)
+    b = xstar_t(yaug - sigma(w))
+    return dict(b=b, w=w, iters=iters, status=status, relres=relres)
+
+
+# ----------------------------------------------------------------------------
+# residuals and the adjoint (gradient) of the augmented-system solution
+# ----------------------------------------------------------------------------
+
+def augmented_residual(X_blocks, Omega, Y, w, b):
+    """Residual of eq. (aug1): (y - Sigma w - X b,  -X^T w), using the SUR
+    applies (no dense matrices), for checks at any size."""
+    op = SurOps.__new__(SurOps)
+    op.X = X_blocks
+    op.Omega = np.asarray(Omega, dtype=float)
+    op.G = len(X_blocks)
+    op.M = X_blocks[0].shape[0]
+    op.n_i = [x.shape[1] for x in X_blocks]
+    op.offs = np.cumsum([0] + op.n_i)
+    m = op.G * op.M
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    w = np.asarray(w, dtype=float).reshape(m, -1)
+    b = np.asarray(b, dtype=float).reshape(int(op.offs[-1]), -1)
+    return Y - op.sigma(w) - op.xmul(b), -op.xt(w)
+
+
+def sur_gls_gradient(X_blocks, Omega, Y, dL_db):
+    """Adjoint of the augmented-system solution (dense, tiny sizes).
+
+    With K = [[Sigma, X], [X^T, 0]] symmetric, (w; b) = K^-1 (y; 0) and a loss
+    L(b):  (lam; mu) = K^-1 (0; dL/db),  dL/dy = lam,  dL/dK = -(lam; mu)(w; b)^T.
+    Sigma = Omega (x) I_M puts omega_ij on the diagonal of block (i, j), so
+    dL/domega_ij = -sum_t Lam[t, i] W[t, j]  (Lam, W the M x G matrices with
+    vec(Lam) = lam, vec(W) = w).  Returns (dL_dy (m, k), dL_dOmega (G, G),
+    unsymmetrised, summed over right-hand sides)."""
+    Sigma, X = sur_dense(X_blocks, Omega)
+    m, n = X.shape
+    G = len(X_blocks)
+    M = m // G
+    K = augmented_matrix(Sigma, X)
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    gb = np.asarray(dL_db, dtype=float).reshape(n, -1)
+    H = np.vstack([Y, np.zeros((n, Y.shape[1]))])
+    x = np.linalg.solve(K, H)
+    adj = np.linalg.solve(K, np.vstack([np.zeros((m, gb.shape[1])), gb]))
+    lam = adj[:m]
+    w = x[:m]
+    gO = np.zeros((G, G))
+    for c in range(Y.shape[1]):
+        Lm = lam[:, c].reshape(G, M).T
+        Wm = w[:, c].reshape(G, M).T
+        gO -= Lm.T @ Wm
+    return lam, gO
