@@ -1,0 +1,368 @@
+"""Benchmark: SUR GLS solves/sec at <= 1e-9 relative error on the singular
+SUR workload (G = 64 equations, M = 20000 observations, n_i ~ U{8..32},
+Omega = A A^T with A 64 x 56, k = 16 right-hand sides), float32-bulk PCG-Aug
+inside float64 iterative refinement, on one GB300.
+
+One step = one complete glm_sur_solve call (all k right-hand sides) with the
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica (the single-instance path
+has no exchange step: replicas only, weak scaling); value = total solves/s.
+--impl reference times the float64 CPU oracle (the reference PCG of the
+paper's algorithm) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SUR GLS solves/sec @ <=1e-9 rel err vs FP64 oracle; PCG-iter HBM GB/s vs roofline"
+WORKLOAD = "sur-singular-g64-m20000-k16 (G=64, M=20000, n_i~U{8..32}, Omega=AA^T rank 56)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--M", type=int, default=20000)
+    ap.add_argument("--G", type=int, default=64)
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 PCG comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(args):
+    from synth import sur_inputs as S
+    return S.config1(k=args.k, M=args.M, G=args.G)
+
+
+def rel_err(b, ref):
+    return float(np.max(np.linalg.norm(b - ref, axis=0) / np.linalg.norm(ref, axis=0)))
+
+
+def oracle_iteration_sample(p, n_iter):
+    """Time n_iter steps of the float64 reference PCG of the oracle (all host
+    cores); returns seconds per step (setup QR excluded)."""
+    from oracle import sur_oracle as O
+    ops = O.SurOps(p.X_blocks, p.Omega)
+    O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=0.0, maxit=2, stag_window=10 ** 9, ops=ops)   # warm
+    t0 = time.perf_counter()
+    O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=0.0, maxit=n_iter, stag_window=10 ** 9, ops=ops)
+    return (time.perf_counter() - t0) / n_iter
+
+
+def oracle_iters_per_solve():
+    path = os.path.join(ROOT, "tests", "golden", "cfg1_oracle_iterations.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return int(max(d["iters"])), "oracle float64 PCG to tol 1e-12 (tests/golden/cfg1_oracle_iterations.json)"
+    return None, None
+
+
+def run_reference(args, rank, world, pg):
+    """CPU reference arm: the oracle's float64 PCG timed on the host cores."""
+    if rank != 0:
+        return 0
+    p = make_problem(args)
+    iters, src = oracle_iters_per_solve()
+    n_iter = 8
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = oracle_iteration_sample(p, n_iter)
+        if s >= args.warmup:
+            times.append(t)
+    t_iter = float(np.mean(times))
+    if iters is None:
+        iters, src = 500, "assumed 500 iterations per solve (no stored oracle count)"
+    sps = 1.0 / (t_iter * iters)
+    line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * iters * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "k": args.k, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n_iter} float64 reference-PCG steps per timed step, "
+                                       f"x {iters} steps per solve ({src})"},
+            "e2e": {"value": sps, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, rank, world, local, pg):
+    import torch
+    from paper_2510_14471_gb300 import build
+    if rank == 0:
+        build.build()
+    if pg is not None:
+        pg.barrier()
+    from paper_2510_14471_gb300 import _lib as L
+    from paper_2510_14471_gb300.sur import GlmSur
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = make_problem(args)
+    m, n, k = p.m, p.n, p.k
+    stream = torch.cuda.current_stream().cuda_stream
+
+    # ---- setup (TSQR), timed separately
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = GlmSur(p.X_blocks, p.Omega, precision=args.precision, tol=1e-12, device=dev)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3   # includes the host->device copy of X
+    Ycm = torch.as_tensor(p.Y.T.copy(), device=dev)                # column-major m x k
+    b = torch.empty((k, n), dtype=torch.float64, device=dev)
+    iters = torch.zeros(k, dtype=torch.int32, device=dev)
+    relres = torch.zeros(k, dtype=torch.float64, device=dev)
+
+    def solve():
+        L.glm_sur_solve(h.handle, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(),
+                        stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    status = L.glm_sur_get_status(h.handle, k)
+    err = rel_err(b.t().cpu().numpy(), p.beta)
+    it_used = iters.cpu().numpy()
+    launches0 = L.glm_sur_launch_count(h.handle)
+
+    # ---- timed region: K solves, inputs resident in HBM (working set > L2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            solve()
+        ev1.record()
+        torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = L.glm_sur_launch_count(h.handle) - launches0
+    if pg is not None:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1e3 / ms
+
+    # ---- end to end through the public API with host buffers
+    Y_host = torch.as_tensor(p.Y.T.copy()).pin_memory()
+    b_host = torch.empty((k, n), dtype=torch.float64).pin_memory()
+    Ydev2 = torch.empty_like(Ycm)
+    e2e_times = []
+    for s in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ydev2.copy_(Y_host, non_blocking=True)
+        L.glm_sur_solve(h.handle, Ydev2.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(),
+                        stream)
+        b_host.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_err = rel_err(b_host.t().numpy(), p.beta)
+    e2e_sps = world / float(np.mean(e2e_times))
+
+    # ---- per-kernel times of one float32 bulk step (dominant kernel roofline)
+    prof = L.glm_sur_profile_steps(h.handle, args.profile_reps, stream)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    pb = 4 if args.precision == "fp32_refine" else 8
+    M, G = args.M, args.G
+    mk = m * k
+    kbytes = {   # algorithmic bytes per launch of each kernel of a step
+        "sigma_step": 6 * pb * mk,                 # read g, u, w; write u, w, S
+        "proj_partial": pb * M * n + pb * mk,      # read Q, S
+        "reduce": 0,
+        "proj_update": pb * M * n + 3 * pb * mk,   # read Q, S, g; write g
+    }
+    names = ["sigma_step", "proj_partial", "reduce", "proj_update"]
+    dom = max(range(4), key=lambda i: prof[i])
+    dname = names[dom]
+    ach = kbytes[dname] / (prof[dom] * 1e-3) / 1e9
+    b_iter = 2 * pb * M * n + 8 * pb * mk
+    ach_iter = b_iter / (prof[4] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(f"{dname}:{args.precision}:k{k}")
+        except Exception:
+            traffic = None
+
+    # ---- float64 PCG on the same workload (comparison at the same accuracy)
+    fp64 = None
+    if not args.no_fp64:
+        h64 = GlmSur(p.X_blocks, p.Omega, precision="fp64", tol=1e-12, device=dev)
+        Lh = h64.handle
+        L.glm_sur_solve(Lh, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(), stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.glm_sur_solve(Lh, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(), stream)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        it64 = iters.cpu().numpy()
+        prof64 = L.glm_sur_profile_steps(Lh, 5, stream)
+        fp64 = {"solves_per_s": 1e3 / t64, "ms_per_solve": t64, "iters_max": int(it64.max()),
+                "rel_err_vs_beta_true": rel_err(b.t().cpu().numpy(), p.beta),
+                "status": L.glm_sur_get_status(Lh, k),
+                "step_ms": prof64[4],
+                "step_fp64_gflops": (2 * M * G * G * k + 4 * M * n * k) / (prof64[4] * 1e-3) / 1e9}
+        h64.close()
+
+    # ---- CPU oracle baseline (rank 0, bounded sample)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_iter = 6
+        t_iter = oracle_iteration_sample(p, n_iter)
+        iters_ref, src = oracle_iters_per_solve()
+        if iters_ref is None and fp64 is not None:
+            iters_ref, src = fp64["iters_max"], "float64 PCG step count of this run"
+        if iters_ref is None:
+            iters_ref, src = 500, "assumed"
+        cpu = {"value": 1.0 / (t_iter * iters_ref), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n_iter} steps of the float64 reference PCG (numpy, k={k}) timed, "
+                         f"x {iters_ref} steps per solve ({src}); setup QR excluded",
+               "sec_per_step": t_iter}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "G": G, "M": M, "n": n, "k": k, "precision": args.precision,
+                       "tol": 1e-12, "l2": "inputs larger than L2 (Q 205 MB f64 + 102 MB f32, vectors 82-164 MB)",
+                       "parallelism": f"replicas{world}"},
+            "per_rhs_solves_per_s": value * k,
+            "rel_err_max": err, "status": status, "iters_max": int(it_used.max()),
+            "setup_ms": setup_ms,
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": traffic, "peak_source": peak_src,
+                         "algorithmic_bytes": kbytes[dname], "ms": prof[dom]},
+            "roofline_iter": {"bound": "hbm", "achieved": ach_iter, "peak": hbm, "unit": "GB/s",
+                              "frac": ach_iter / hbm, "B_iter": b_iter, "ms": prof[4],
+                              "kernel_ms": dict(zip(names, prof[:4]))},
+            "fp64_pcg": fp64,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_sps, "unit": "solves/s", "h2d_bytes_per_step": int(m * k * 8),
+                    "d2h_bytes_per_step": int(n * k * 8), "rel_err_max": e2e_err},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    h.close()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_init(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world, pg)
+        return run_ours(args, rank, world, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

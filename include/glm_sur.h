@@ -1,0 +1,170 @@
+/*
+ * glm_sur.h -- C ABI of the GB300 (sm_103a) library for GLS estimation of
+ * Seemingly Unrelated Regressions (SUR) models by PCG-Aug.
+ *
+ * The method (Foschi, "Preconditioned Conjugate Gradient methods for the
+ * estimation of General Linear Models"):
+ *   SUR model (Sec. 1, eq. SURdefs):  y = vec(Y),  X = (+)_i X_i (M x n_i blocks),
+ *                                      Sigma = Omega (x) I_M,  Omega G x G, PSD.
+ *   GLS as the augmented system eq. (aug1):  [Sigma X; X^T 0][w; b] = [y; 0].
+ *   Solved by Algorithm glmpcg2 (PCG-Aug) with the indefinite preconditioner
+ *   eq. (invprec) and D = I (Sec. 5.3): every step applies Sigma as U * Omega
+ *   and the per-block OLS projection Pi_i = I - Q_i Q_i^T from a Householder
+ *   QR X_i = Q_i R_i computed once; the estimate is z = X*^T (y - Sigma w)
+ *   with X*^T xi = vec(R_i^-1 Q_i^T xi_i).
+ *
+ * Conventions common to every entry point
+ *   - All matrix arguments are DEVICE pointers to float64 data in column-major
+ *     order unless stated otherwise; the caller owns them and they need only be
+ *     valid for the duration of the call (work is stream-ordered: "the call"
+ *     ends when the stream reaches it).  Outputs are written into caller
+ *     buffers.  The handle owns every other allocation.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is asynchronous with respect to the host except where noted.
+ *   - The return value reports host-side validation, allocation and launch
+ *     errors.  Conditions found on the device (rank deficiency, breakdown,
+ *     stagnation, non-convergence, non-finite data) are written to the
+ *     per-right-hand-side status array and read with glm_sur_get_status.
+ *   - No exception crosses the ABI.  A handle must not be used from two host
+ *     threads at once; different handles are independent.
+ */
+#ifndef GLM_SUR_H
+#define GLM_SUR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* glm_sur_stream_t;   /* == cudaStream_t */
+
+typedef struct glm_sur_ctx* glm_sur_t;          /* opaque handle */
+
+typedef enum {
+  GLM_SUR_OK = 0,
+  GLM_SUR_INVALID_ARG = 1,     /* bad size, null pointer, unsupported option      */
+  GLM_SUR_RANK_DEFICIENT = 2,  /* some X_i not of full column rank (|R_jj| tiny)   */
+  GLM_SUR_BREAKDOWN = 3,       /* d_i = u^T Sigma u <= 0 or not finite (Sec. 2)    */
+  GLM_SUR_STAGNATED = 4,       /* c_i = r^T Pi r stopped decreasing (Sec. 3.2)     */
+  GLM_SUR_NOT_CONVERGED = 5,   /* maxit reached                                    */
+  GLM_SUR_TIMEOUT = 6,         /* a bounded device wait gave up                    */
+  GLM_SUR_NONFINITE = 7,       /* NaN/Inf in inputs                                */
+  GLM_SUR_OOM = 8,             /* device allocation failed                         */
+  GLM_SUR_CUDA_ERROR = 9       /* a CUDA runtime call failed                       */
+} glm_sur_status;
+
+enum {
+  GLM_SUR_PREC_FP64 = 0,          /* every step in float64                          */
+  GLM_SUR_PREC_FP32_REFINE = 1    /* float32 bulk iterations inside a float64
+                                     iterative-refinement loop                     */
+};
+
+typedef struct {
+  int precision;          /* GLM_SUR_PREC_*                                         */
+  double tol;             /* stop a column when sqrt(c_i / c_1) <= tol              */
+  int maxit;              /* iteration cap of one PCG run (<= 0: m - n + 1)         */
+  int stagnation_window;  /* W: stagnated if c_i >= c_{i-W} (<= 0: 10)              */
+  double inner_tol;       /* FP32_REFINE: relative reduction per inner solve        */
+  int max_refine;         /* FP32_REFINE: cap on outer (refinement) steps           */
+  int chunk;              /* iterations per captured CUDA graph launch (even, >= 2) */
+  double inner_shift;     /* FP32_REFINE: the inner solves use Omega + s I with
+                             s = inner_shift * max_i omega_ii (0 disables); the
+                             float64 residual always uses Omega itself        */
+} glm_sur_opts;
+
+/* Default options: FP64, tol 1e-12, maxit m-n+1, W = 10, inner_tol 1e-5,
+ * max_refine 8, chunk 16, inner_shift 1e-6. */
+void glm_sur_default_opts(glm_sur_opts* opts);
+
+/*
+ * glm_sur_setup -- factor the regressors once (Sec. 3.2, "auxiliary GLM per
+ * step": the factorisations are computed once; Sec. 5.3: X_i = Q_i R_i).
+ *
+ *   out    : receives the new handle (host pointer).
+ *   G      : number of equations (>= 1).
+ *   M      : observations per equation (>= max n_i).
+ *   n_i    : HOST array of G block widths, 1 <= n_i <= 64.
+ *   X      : DEVICE, M x n column-major with leading dimension ldx >= M,
+ *            n = sum n_i; columns offs_i .. offs_i + n_i - 1 hold X_i
+ *            (i.e. X = [X_1 ... X_G] = W of Remark rem:reduction).
+ *   Omega  : DEVICE, G x G symmetric positive semi-definite (Sec. 1).
+ *   opts   : HOST, may be NULL for defaults.
+ * The handle keeps Q_i (explicit thin factor, M x n_i), R_i and Omega.
+ * Errors: INVALID_ARG on bad sizes; OOM; CUDA_ERROR.  Rank deficiency of an
+ * X_i is detected on the device and reported by glm_sur_get_setup_status.
+ */
+glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i,
+                             const double* X, int64_t ldx, const double* Omega,
+                             const glm_sur_opts* opts, glm_sur_stream_t stream);
+
+/* Synchronises the handle's last setup and returns GLM_SUR_OK or
+ * GLM_SUR_RANK_DEFICIENT (a block with |R_jj| <= n_i * eps * max|R|). */
+glm_sur_status glm_sur_get_setup_status(glm_sur_t h);
+
+/* Replace Omega (DEVICE, G x G) without refactoring X (Sec. 5.3: the QRs
+ * depend on X only). */
+glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_stream_t stream);
+
+/* Replace the options used by later solves. */
+glm_sur_status glm_sur_set_opts(glm_sur_t h, const glm_sur_opts* opts);
+
+/*
+ * glm_sur_solve -- Algorithm glmpcg2 (PCG-Aug) with D = I, one independent PCG
+ * per right-hand side, started at w_1 = 0, z_1 = 0; returns
+ * b = z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
+ *
+ *   Y      : DEVICE, m x k column-major (m = G*M), column j = vec(Y_j),
+ *            leading dimension ldy >= m.
+ *   k      : number of right-hand sides, 1 <= k <= 64.
+ *   b      : DEVICE output, n x k column-major, leading dimension ldb >= n.
+ *   iters  : DEVICE output (nullable), k ints: PCG steps taken per column
+ *            (summed over inner solves for FP32_REFINE).
+ *   relres : DEVICE output (nullable), k doubles: final sqrt(c/c_1) per column
+ *            (FP32_REFINE: the float64 true residual ||P(y - Sigma w)|| / ||P y||).
+ * The final w (float64, m x k) stays in the handle for glm_sur_backward.
+ * FP32_REFINE synchronises the stream once per refinement step.
+ */
+glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k,
+                             double* b, int64_t ldb, int* iters, double* relres,
+                             glm_sur_stream_t stream);
+
+/* Synchronises and copies the per-column status of the last solve (k values,
+ * glm_sur_status codes) into the HOST array `status`. */
+glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k);
+
+/* Copies the float64 w of the last solve (m x k column-major, DEVICE, ldw >= m)
+ * into a caller buffer; Sigma w is the GLM residual of eq. (aug1). */
+glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream);
+
+/* Copies the factors of glm_sur_setup into caller buffers (both DEVICE):
+ * Q (M x n column-major, ldq >= M): the thin Q_i side by side, [Q_1 ... Q_G];
+ * R (sum_i n_i^2 doubles): R_i row-major n_i x n_i, blocks in order.
+ * Either pointer may be NULL. */
+glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* R, glm_sur_stream_t stream);
+
+/* Number of kernel launches (including the nodes of replayed CUDA graphs)
+ * this handle has issued since glm_sur_setup.  Host-side counter. */
+int64_t glm_sur_launch_count(glm_sur_t h);
+
+/* Measurement helper.  Runs `reps` PCG steps of the configuration of the last
+ * solve (same k and precision; float32 bulk steps for FP32_REFINE) on the
+ * handle's buffers, with the stop tests disabled, and writes the mean device
+ * time in milliseconds of each launch of one step into the HOST array ms[5]:
+ * ms[0] Sigma-apply step, ms[1] projection partials, ms[2] reduction and
+ * scalar step, ms[3] projection update, ms[4] the whole step.  Events are
+ * recorded on `stream`.  Synchronous.  Destroys the stored w (glm_sur_get_w
+ * fails until the next solve). */
+glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_stream_t stream);
+
+void glm_sur_destroy(glm_sur_t h);
+const char* glm_sur_status_string(glm_sur_status s);
+
+/* Library build information (static string). */
+const char* glm_sur_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLM_SUR_H */

@@ -278,10 +278,11 @@ class SurOps:
         self.QR = [np.linalg.qr(Xi) for Xi in X_blocks]
 
     def sigma(self, u):
+        # (U Omega)_h = sum_g U_g omega_gh: with the G columns of every U_j as
+        # the rows of a (G, M*k) matrix this is one matrix product Omega^T U.
         k = u.shape[1]
-        U = u.reshape(self.G, self.M, k)                      # U[i] = column i of each U_j
-        S = np.einsum("gh,gmk->hmk", self.Omega, U)           # (U Omega)_h = sum_g U_g w_gh
-        return S.reshape(self.G * self.M, k)
+        U = u.reshape(self.G, self.M * k)
+        return (self.Omega.T @ U).reshape(self.G * self.M, k)
 
     def pi(self, xi):
         out = np.empty_like(xi)
@@ -327,8 +328,10 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=10,
     large range-space part of r against Pi r (which floors sqrt(c/c_1) near
     sqrt(eps) when written as r . (Pi r)).
     Stop a column when sqrt(c_{i+1}/c_1) <= tol (converged), when d_i <= 0 or
-    is not finite (breakdown), when c_{i+1} >= c_{i+1-W} over a window of W
-    steps (stagnation), or at ``maxit``.  Always return
+    is not finite (breakdown), when c has not reached a new minimum for W
+    steps (stagnation: "not anymore able to decrease", Sec. 3.2; c_i need
+    not decrease monotonically, so a window over the running minimum is
+    used), or at ``maxit``.  Always return
     z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
     Returns dict(b, w, iters, status, relres[, history])."""
     op = ops if ops is not None else SurOps(X_blocks, Omega)
@@ -351,7 +354,8 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=10,
     status = np.array([STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active],
                       dtype=object)
     relres = np.where(c1 > 0, 1.0, 0.0)
-    chist = [c.copy()]
+    cbest = c.copy()
+    itbest = np.zeros(k, dtype=int)
     hist = {"w": [w.copy()], "r": [r.copy()], "u": [u.copy()], "c": [c.copy()]} if record else None
     for it in range(1, maxit + 1):
         if not active.any():
@@ -368,18 +372,23 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=10,
         Pr = op.pi(r)
         c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)  # step 8
         iters = iters + active
-        chist.append(c_new.copy())
         rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
         relres = np.where(active, rr, relres)
+        bad_c = active & (~np.isfinite(c_new) | (c_new < 0))
+        for j in np.where(bad_c)[0]:
+            status[j] = STATUS_BREAKDOWN
+        active &= ~bad_c
         conv = active & (rr <= tol)
         for j in np.where(conv)[0]:
             status[j] = STATUS_CONVERGED
         active &= ~conv
-        if it > stag_window:
-            stag = active & (c_new >= chist[-1 - stag_window])
-            for j in np.where(stag)[0]:
-                status[j] = STATUS_STAGNATED
-            active &= ~stag
+        better = active & (c_new < cbest)
+        cbest = np.where(better, c_new, cbest)
+        itbest = np.where(better, it, itbest)
+        stag = active & (it - itbest >= stag_window)
+        for j in np.where(stag)[0]:
+            status[j] = STATUS_STAGNATED
+        active &= ~stag
         mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
         v = op.xstar_t(r) + mu * v                            # step 12
         u = np.where(active, Pr + mu * u, u)
@@ -434,9 +443,9 @@ def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=10
         return xi - xmul(xstar_t(xi))
 
     def sigma(u):
-        U = u[:m].reshape(G, M, -1)
-        S = np.einsum("gh,gmk->hmk", Omega, U).reshape(m, -1)
-        return np.vstack([S, np.zeros((kc, u.shape[1]))])
+        kk = u.shape[1]
+        S = (Omega.T @ u[:m].reshape(G, M * kk)).reshape(m, kk)
+        return np.vstack([S, np.zeros((kc, kk))])
 
     if maxit is None:
         maxit = m + kc - n + 1
@@ -451,7 +460,8 @@ def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=10
     iters = np.zeros(k, dtype=int)
     status = [STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active]
     relres = np.where(c1 > 0, 1.0, 0.0)
-    chist = [c.copy()]
+    cbest = c.copy()
+    itbest = np.zeros(k, dtype=int)
     for it in range(1, maxit + 1):
         if not active.any():
             break
@@ -467,18 +477,19 @@ def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=10
         Pr = pi(r)
         c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)
         iters = iters + active
-        chist.append(c_new.copy())
         rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
         relres = np.where(active, rr, relres)
         conv = active & (rr <= tol)
         for j in np.where(conv)[0]:
             status[j] = STATUS_CONVERGED
         active &= ~conv
-        if it > stag_window:
-            stag = active & (c_new >= chist[-1 - stag_window])
-            for j in np.where(stag)[0]:
-                status[j] = STATUS_STAGNATED
-            active &= ~stag
+        better = active & (c_new < cbest)
+        cbest = np.where(better, c_new, cbest)
+        itbest = np.where(better, it, itbest)
+        stag = active & (it - itbest >= stag_window)
+        for j in np.where(stag)[0]:
+            status[j] = STATUS_STAGNATED
+        active &= ~stag
         mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
         v = xstar_t(r) + mu * v
         u = np.where(active, Pr + mu * u, u)

@@ -1,0 +1,760 @@
+// C ABI of the SUR PCG-Aug library: handle, workspace, setup (TSQR), solve
+// (float64 PCG, or float32 bulk inside float64 iterative refinement) and the
+// b recovery of Algorithm glmpcg2 step 10.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "glm_sur.h"
+#include "internal.h"
+#include "pcg.h"
+
+namespace glmsur {
+
+static thread_local std::string g_last_error;
+void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// One cached CUDA graph holding `chunk` PCG steps of one configuration.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int key_prec = -1, key_k = -1, key_chunk = -1;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key_prec = key_k = key_chunk = -1;
+  }
+};
+
+}  // namespace glmsur
+
+using namespace glmsur;
+
+struct glm_sur_ctx {
+  int dev = 0, sms = 148;
+  Geom gm;
+  std::vector<int> n_i, off, poff;
+  glm_sur_opts opts;
+  // factors
+  double* Q64 = nullptr;
+  float* Q32 = nullptr;
+  double* R = nullptr;
+  double* Om64 = nullptr;
+  float* Om32 = nullptr;
+  int* setup_flags = nullptr;
+  // solve workspace (capacity kcap right-hand sides)
+  int kcap = 0;
+  double *y64 = nullptr, *w64 = nullptr, *g64 = nullptr, *u64 = nullptr, *S64 = nullptr, *E64 = nullptr;
+  float *g32 = nullptr, *u32 = nullptr, *w32 = nullptr, *S32 = nullptr;
+  double* d64 = nullptr;        // last projected refinement correction
+  int* d_mask = nullptr;        // 2 x k column masks (live columns, columns to revert)
+  void* Cpart = nullptr;
+  void* Cfin = nullptr;
+  double* C64 = nullptr;
+  double *dpart = nullptr, *cpart = nullptr, *norms = nullptr;
+  // PCG state arrays
+  double* st_buf = nullptr;
+  int* st_ibuf = nullptr;
+  PcgState st;
+  int* h_done = nullptr;           // pinned
+  double* h_norms = nullptr;       // pinned
+  int last_k = 0;
+  int* h_status = nullptr;         // host copy of the last per-column status (k)
+  int* d_status_final = nullptr;   // device per-column final status
+  int* d_iters_acc = nullptr;      // accumulated iterations (refinement)
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  StepGraph graph;
+  IterPlan plan;
+  int plan_k = -1, plan_prec = -1;
+  bool has_w = false;
+  int64_t launches = 0;        // kernel launches issued (graph nodes included)
+};
+
+namespace {
+
+constexpr int kStateDoubles = 7;
+constexpr int kStateInts = 6;
+constexpr int kInnerStagnation = 25;   // stagnation window of the float32 inner solves
+
+glm_sur_status validate_opts(const glm_sur_opts* o) {
+  if (o->precision != GLM_SUR_PREC_FP64 && o->precision != GLM_SUR_PREC_FP32_REFINE) return GLM_SUR_INVALID_ARG;
+  if (!(o->tol >= 0.0) || !(o->inner_tol > 0.0)) return GLM_SUR_INVALID_ARG;
+  if (o->chunk < 2 || (o->chunk & 1)) return GLM_SUR_INVALID_ARG;
+  if (!(o->inner_shift >= 0.0) || o->inner_shift > 1e-2) return GLM_SUR_INVALID_ARG;
+  return GLM_SUR_OK;
+}
+
+int pick_jj(int k, bool is_double) {
+  const int cap = is_double ? 8 : 16;
+  for (int jj = cap; jj > 1; jj >>= 1)
+    if (k % jj == 0) return jj;
+  return 1;
+}
+
+glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
+  const Geom& gm = h->gm;
+  const size_t sz = is_double ? 8 : 4;
+  p.JJ = pick_jj(k, is_double);
+  const int njg = k / p.JJ;
+  const size_t om_bytes = sz * (size_t)gm.G * gm.Gq;
+  const size_t row_bytes = sz * (size_t)gm.G * p.JJ;
+  const size_t budget = 200 * 1024;
+  if (om_bytes + row_bytes > budget) return GLM_SUR_INVALID_ARG;   // G too large for the Sigma tile
+  p.TR = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / 2 - std::min(om_bytes, budget / 2)) / row_bytes));
+  if (p.TR < 1) p.TR = 1;
+  p.sigma_smem = om_bytes + (size_t)p.TR * row_bytes;
+  const int target = 2 * h->sms;
+  p.n_sigma = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(gm.M, p.TR), ceil_div(target, njg)));
+  p.n_qgroups = (int)std::max<int64_t>(1, ceil_div(gm.nq, 256));
+  p.n_partial_rows = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, (int64_t)p.n_qgroups * njg)));
+  p.n_update = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, njg)));
+  cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem) : set_smem_attrs<float>(p.JJ, p.sigma_smem);
+  if (e != cudaSuccess) {
+    set_last_error(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    return GLM_SUR_CUDA_ERROR;
+  }
+  return GLM_SUR_OK;
+}
+
+void free_workspace(glm_sur_ctx* h) {
+  dfree(h->y64); dfree(h->w64); dfree(h->g64); dfree(h->u64); dfree(h->S64); dfree(h->E64);
+  dfree(h->g32); dfree(h->u32); dfree(h->w32); dfree(h->S32);
+  if (h->Cpart) cudaFree(h->Cpart);
+  if (h->Cfin) cudaFree(h->Cfin);
+  h->Cpart = h->Cfin = nullptr;
+  dfree(h->C64); dfree(h->dpart); dfree(h->cpart); dfree(h->norms);
+  dfree(h->st_buf); dfree(h->st_ibuf); dfree(h->d_status_final); dfree(h->d_iters_acc);
+  dfree(h->d64); dfree(h->d_mask);
+  if (h->h_status) { delete[] h->h_status; h->h_status = nullptr; }
+  h->kcap = 0;
+  h->graph.reset();
+}
+
+// Allocate every buffer a solve with k right-hand sides needs (both precisions).
+glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
+  if (k <= h->kcap) return GLM_SUR_OK;
+  free_workspace(h);
+  const Geom& gm = h->gm;
+  const size_t mk = (size_t)gm.M * gm.G * k;
+  const int maxrows = 2 * h->sms;   // upper bound of every row-CTA count in make_plan
+  const size_t cpart_n = (size_t)maxrows * gm.np * k;
+  GS_CUDA_TRY(dalloc(&h->y64, mk));
+  GS_CUDA_TRY(dalloc(&h->w64, mk));
+  GS_CUDA_TRY(dalloc(&h->g64, mk));
+  GS_CUDA_TRY(dalloc(&h->E64, mk));
+  if (h->opts.precision == GLM_SUR_PREC_FP64) {
+    GS_CUDA_TRY(dalloc(&h->u64, mk));
+    GS_CUDA_TRY(dalloc(&h->S64, mk));
+  } else {
+    GS_CUDA_TRY(dalloc(&h->g32, mk));
+    GS_CUDA_TRY(dalloc(&h->u32, mk));
+    GS_CUDA_TRY(dalloc(&h->w32, mk));
+    GS_CUDA_TRY(dalloc(&h->S32, mk));
+  }
+  GS_CUDA_TRY(cudaMalloc(&h->Cpart, cpart_n * sizeof(double)));
+  GS_CUDA_TRY(cudaMalloc(&h->Cfin, (size_t)gm.np * k * sizeof(double)));
+  GS_CUDA_TRY(dalloc(&h->C64, (size_t)gm.np * k));
+  GS_CUDA_TRY(dalloc(&h->dpart, (size_t)maxrows * k));
+  GS_CUDA_TRY(dalloc(&h->cpart, (size_t)maxrows * k));
+  GS_CUDA_TRY(dalloc(&h->norms, (size_t)2 * k));
+  if (h->opts.precision != GLM_SUR_PREC_FP64) GS_CUDA_TRY(dalloc(&h->d64, mk));
+  // doubles: c[2], c1, lam, relres, cbest[2];  ints: active[2], iters, status, itbest[2], it, done
+  GS_CUDA_TRY(dalloc(&h->st_buf, (size_t)kStateDoubles * k));
+  GS_CUDA_TRY(dalloc(&h->st_ibuf, (size_t)kStateInts * k + 2));
+  GS_CUDA_TRY(dalloc(&h->d_status_final, (size_t)k));
+  GS_CUDA_TRY(dalloc(&h->d_iters_acc, (size_t)k));
+  GS_CUDA_TRY(dalloc(&h->d_mask, (size_t)2 * k));
+  h->h_status = new int[k];
+  PcgState& st = h->st;
+  st.k = k;
+  st.c[0] = h->st_buf;
+  st.c[1] = h->st_buf + k;
+  st.c1 = h->st_buf + 2 * k;
+  st.lam = h->st_buf + 3 * k;
+  st.relres = h->st_buf + 4 * k;
+  st.cbest[0] = h->st_buf + 5 * k;
+  st.cbest[1] = h->st_buf + 6 * k;
+  st.active[0] = h->st_ibuf;
+  st.active[1] = h->st_ibuf + k;
+  st.iters = h->st_ibuf + 2 * k;
+  st.status = h->st_ibuf + 3 * k;
+  st.itbest[0] = h->st_ibuf + 4 * k;
+  st.itbest[1] = h->st_ibuf + 5 * k;
+  st.it = h->st_ibuf + 6 * k;
+  st.done = h->st_ibuf + 6 * k + 1;
+  h->kcap = k;
+  return GLM_SUR_OK;
+}
+
+// Reset the per-column PCG state before a run (stream-ordered).
+glm_sur_status reset_state(glm_sur_ctx* h, int k, double tol, int maxit, int W, cudaStream_t s) {
+  PcgState& st = h->st;
+  st.k = k;
+  st.tol = tol;
+  st.maxit = maxit;
+  st.W = W;
+  GS_CUDA_TRY(cudaMemsetAsync(h->st_buf, 0, sizeof(double) * (size_t)kStateDoubles * h->kcap, s));
+  GS_CUDA_TRY(cudaMemsetAsync(h->st_ibuf, 0, sizeof(int) * ((size_t)kStateInts * h->kcap + 2), s));
+  return GLM_SUR_OK;
+}
+
+template <typename T>
+struct Bufs;
+template <>
+struct Bufs<double> {
+  static double* g(glm_sur_ctx* h) { return h->g64; }
+  static double* u(glm_sur_ctx* h) { return h->u64; }
+  static double* w(glm_sur_ctx* h) { return h->w64; }
+  static double* S(glm_sur_ctx* h) { return h->S64; }
+  static double* Q(glm_sur_ctx* h) { return h->Q64; }
+  static double* Om(glm_sur_ctx* h) { return h->Om64; }
+};
+template <>
+struct Bufs<float> {
+  static float* g(glm_sur_ctx* h) { return h->g32; }
+  static float* u(glm_sur_ctx* h) { return h->u32; }
+  static float* w(glm_sur_ctx* h) { return h->w32; }
+  static float* S(glm_sur_ctx* h) { return h->S32; }
+  static float* Q(glm_sur_ctx* h) { return h->Q32; }
+  static float* Om(glm_sur_ctx* h) { return h->Om32; }
+};
+
+// Enqueue n PCG steps (four launches each).
+template <typename T>
+void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
+  const IterPlan& p = h->plan;
+  T* Cpart = reinterpret_cast<T*>(h->Cpart);
+  T* C = reinterpret_cast<T*>(h->Cfin);
+  for (int i = 0; i < n; ++i) {
+    launch_sigma_step<T>(p, h->gm, k, Bufs<T>::Om(h), Bufs<T>::g(h), Bufs<T>::u(h), Bufs<T>::w(h), Bufs<T>::S(h),
+                         h->st, h->cpart, h->dpart, s);
+    launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Cpart, h->st, 1, s);
+    launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
+    launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Bufs<T>::g(h), C, 1, h->st.lam, 0.0,
+                          h->cpart, h->st, 1, s);
+  }
+}
+
+// Run PCG steps until every column stopped: a captured graph of `chunk`
+// steps is replayed, and the host reads the done flag one replay behind.
+template <typename T>
+glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int chunk = h->opts.chunk;
+  StepGraph& gr = h->graph;
+  if (!gr.exec || gr.key_prec != prec || gr.key_k != k || gr.key_chunk != chunk) {
+    gr.reset();
+    cudaGraph_t graph = nullptr;
+    GS_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_steps<T>(h, k, chunk, h->cap_stream);
+    GS_CUDA_TRY(cudaStreamEndCapture(h->cap_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&gr.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_last_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+      gr.exec = nullptr;
+      return GLM_SUR_CUDA_ERROR;
+    }
+    gr.key_prec = prec; gr.key_k = k; gr.key_chunk = chunk;
+  }
+  const int64_t max_launch = (int64_t)maxit / chunk + 3;
+  for (int64_t c = 0; c < max_launch; ++c) {
+    GS_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
+    h->launches += 4 * (int64_t)chunk;
+    GS_CUDA_TRY(cudaMemcpyAsync(&h->h_done[c & 1], h->st.done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA_TRY(cudaEventRecord(h->ev[c & 1], s));
+    if (c >= 1) {
+      GS_CUDA_TRY(cudaEventSynchronize(h->ev[(c - 1) & 1]));
+      if (h->h_done[(c - 1) & 1]) break;
+    }
+  }
+  return GLM_SUR_OK;
+}
+
+// g = -P y  (first residual of the PCG started at w = 0), u = w = 0, partials of g^T g.
+template <typename T>
+glm_sur_status pcg_init(glm_sur_ctx* h, int k, const T* y_layout, cudaStream_t s) {
+  const IterPlan& p = h->plan;
+  T* Cpart = reinterpret_cast<T*>(h->Cpart);
+  T* C = reinterpret_cast<T*>(h->Cfin);
+  const size_t mk = (size_t)h->gm.M * h->gm.G * k;
+  launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), y_layout, Cpart, h->st, 0, s);
+  launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 0, nullptr, s);
+  launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), y_layout, Bufs<T>::g(h), C, 0, nullptr, 1.0, h->cpart, h->st, 0,
+                        s);
+  h->launches += 3;
+  GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::u(h), 0, mk * sizeof(T), s));
+  GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::w(h), 0, mk * sizeof(T), s));
+  return GLM_SUR_OK;
+}
+
+// rho = P (y - Sigma w64) in float64 (into g64), partials of rho^T rho in cpart.
+glm_sur_status true_residual(glm_sur_ctx* h, int k, const IterPlan& p64, cudaStream_t s) {
+  double* Cpart = reinterpret_cast<double*>(h->Cpart);
+  launch_sigma_resid<double>(p64, h->gm, k, h->Om64, h->y64, h->w64, h->E64, s);
+  launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+  launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  launch_proj_update<double>(p64, h->gm, k, h->Q64, h->E64, h->g64, h->C64, 0, nullptr, -1.0, h->cpart, h->st, 0, s);
+  h->launches += 4;
+  return GLM_SUR_OK;
+}
+
+// d64 = P (double) w32;  w64 += d64 on the live columns (mask d_mask[0..k))
+glm_sur_status project_correction(glm_sur_ctx* h, int k, const IterPlan& p64, cudaStream_t s) {
+  double* Cpart = reinterpret_cast<double*>(h->Cpart);
+  const int64_t mk = h->gm.M * h->gm.G * k;
+  launch_convert<float, double>(mk, h->w32, h->E64, 1.0, s);
+  launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+  launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  launch_proj_update<double>(p64, h->gm, k, h->Q64, h->E64, h->d64, h->C64, 0, nullptr, -1.0, h->cpart, h->st, 0, s);
+  launch_masked_axpy(mk, k, h->d_mask, 1.0, h->d64, h->w64, s);
+  h->launches += 5;
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
+// b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 5.3)
+glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, int64_t ldb, cudaStream_t s) {
+  double* Cpart = reinterpret_cast<double*>(h->Cpart);
+  launch_sigma_resid<double>(p64, h->gm, k, h->Om64, h->y64, h->w64, h->E64, s);
+  launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+  launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  launch_tri_solve(h->gm, k, h->R, h->C64, b, ldb, s);
+  h->launches += 4;
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void glm_sur_default_opts(glm_sur_opts* o) {
+  if (!o) return;
+  o->precision = GLM_SUR_PREC_FP64;
+  o->tol = 1e-12;
+  o->maxit = 0;
+  o->stagnation_window = 10;
+  o->inner_tol = 1e-5;
+  o->max_refine = 8;
+  o->chunk = 16;
+  o->inner_shift = 1e-6;
+}
+
+const char* glm_sur_status_string(glm_sur_status s) {
+  switch (s) {
+    case GLM_SUR_OK: return "ok";
+    case GLM_SUR_INVALID_ARG: return "invalid argument";
+    case GLM_SUR_RANK_DEFICIENT: return "rank deficient regressor block";
+    case GLM_SUR_BREAKDOWN: return "PCG breakdown (d <= 0 or not finite)";
+    case GLM_SUR_STAGNATED: return "PCG stagnated";
+    case GLM_SUR_NOT_CONVERGED: return "maximum iterations reached";
+    case GLM_SUR_TIMEOUT: return "device wait timed out";
+    case GLM_SUR_NONFINITE: return "non-finite input";
+    case GLM_SUR_OOM: return "out of device memory";
+    case GLM_SUR_CUDA_ERROR: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
+  }
+  return "unknown status";
+}
+
+const char* glm_sur_version(void) { return "glm_sur 0.1 (sm_103a, PCG-Aug SUR)"; }
+
+glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, const double* X, int64_t ldx,
+                             const double* Omega, const glm_sur_opts* opts, glm_sur_stream_t stream) {
+  if (!out || !n_i || !X || !Omega) return GLM_SUR_INVALID_ARG;
+  *out = nullptr;
+  if (G < 1 || G > kMaxG || M < 1 || ldx < M) return GLM_SUR_INVALID_ARG;
+  int nmax = 0;
+  for (int i = 0; i < G; ++i) {
+    if (n_i[i] < 1 || n_i[i] > kMaxBlockCols) return GLM_SUR_INVALID_ARG;
+    nmax = std::max(nmax, n_i[i]);
+  }
+  if (M < nmax) return GLM_SUR_INVALID_ARG;
+  glm_sur_opts o;
+  glm_sur_default_opts(&o);
+  if (opts) o = *opts;
+  if (validate_opts(&o) != GLM_SUR_OK) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  glm_sur_ctx* h = new glm_sur_ctx();
+  h->opts = o;
+  cudaGetDevice(&h->dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  Geom& gm = h->gm;
+  gm.G = G;
+  gm.Gq = round_up4(G);
+  gm.M = M;
+  h->n_i.assign(n_i, n_i + G);
+  h->off.assign(G + 1, 0);
+  h->poff.assign(G + 1, 0);
+  std::vector<int> quad_blk;
+  std::vector<int64_t> r_off(G + 1, 0);
+  for (int i = 0; i < G; ++i) {
+    h->off[i + 1] = h->off[i] + n_i[i];
+    h->poff[i + 1] = h->poff[i] + round_up4(n_i[i]);
+    for (int q = 0; q < round_up4(n_i[i]) / 4; ++q) quad_blk.push_back(i);
+    r_off[i + 1] = r_off[i] + (int64_t)n_i[i] * n_i[i];
+  }
+  gm.n = h->off[G];
+  gm.np = h->poff[G];
+  gm.nq = gm.np / 4;
+  glm_sur_status rc = GLM_SUR_OK;
+  auto bail = [&](glm_sur_status r) {
+    glm_sur_destroy(h);
+    return r;
+  };
+#define SETUP_TRY(expr)                                            \
+  do {                                                             \
+    cudaError_t e_ = (expr);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      set_last_error(e_, #expr, __FILE__, __LINE__);               \
+      return bail(e_ == cudaErrorMemoryAllocation ? GLM_SUR_OOM : GLM_SUR_CUDA_ERROR); \
+    }                                                              \
+  } while (0)
+  SETUP_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  SETUP_TRY(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+  SETUP_TRY(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+  SETUP_TRY(cudaMallocHost(&h->h_done, 2 * sizeof(int)));
+  SETUP_TRY(cudaMallocHost(&h->h_norms, 2 * kMaxRhs * sizeof(double)));
+  SETUP_TRY(dalloc(&gm.d_n_i, G));
+  SETUP_TRY(dalloc(&gm.d_off, G + 1));
+  SETUP_TRY(dalloc(&gm.d_poff, G + 1));
+  SETUP_TRY(dalloc(&gm.d_quad_blk, gm.nq));
+  SETUP_TRY(dalloc(&gm.d_r_off, G + 1));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_n_i, n_i, G * sizeof(int), cudaMemcpyHostToDevice, s));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_off, h->off.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_poff, h->poff.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_quad_blk, quad_blk.data(), gm.nq * sizeof(int), cudaMemcpyHostToDevice, s));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_r_off, r_off.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SETUP_TRY(dalloc(&h->Q64, (size_t)M * gm.np));
+  SETUP_TRY(dalloc(&h->R, (size_t)r_off[G]));
+  SETUP_TRY(dalloc(&h->Om64, (size_t)G * gm.Gq));
+  SETUP_TRY(dalloc(&h->Om32, (size_t)G * gm.Gq));
+  SETUP_TRY(dalloc(&h->setup_flags, 1));
+  SETUP_TRY(cudaMemsetAsync(h->Q64, 0, sizeof(double) * (size_t)M * gm.np, s));
+  SETUP_TRY(cudaMemsetAsync(h->setup_flags, 0, sizeof(int), s));
+  // TSQR of every block
+  QrPlan plan;
+  build_qr_plan(G, M, h->n_i, plan);
+  rc = run_qr(plan, X, ldx, gm.d_off, gm.d_poff, gm.d_r_off, h->Q64, gm.np, h->R, h->setup_flags, s);
+  if (rc != GLM_SUR_OK) return bail(rc);
+  if (o.precision == GLM_SUR_PREC_FP32_REFINE) {
+    SETUP_TRY(dalloc(&h->Q32, (size_t)M * gm.np));
+    launch_convert<double, float>((int64_t)M * gm.np, h->Q64, h->Q32, 1.0, s);
+    SETUP_TRY(cudaGetLastError());
+  }
+  *out = h;
+  rc = glm_sur_set_omega(h, Omega, stream);
+  if (rc != GLM_SUR_OK) {
+    *out = nullptr;
+    return bail(rc);
+  }
+#undef SETUP_TRY
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_get_setup_status(glm_sur_t h) {
+  if (!h) return GLM_SUR_INVALID_ARG;
+  int flags = 0;
+  GS_CUDA_TRY(cudaMemcpy(&flags, h->setup_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flags & 2) return GLM_SUR_NONFINITE;
+  if (flags & 1) return GLM_SUR_RANK_DEFICIENT;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_stream_t stream) {
+  if (!h || !Omega) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const Geom& gm = h->gm;
+  GS_CUDA_TRY(cudaMemsetAsync(h->Om64, 0, sizeof(double) * (size_t)gm.G * gm.Gq, s));
+  GS_CUDA_TRY(cudaMemcpy2DAsync(h->Om64, gm.Gq * sizeof(double), Omega, gm.G * sizeof(double),
+                                gm.G * sizeof(double), gm.G, cudaMemcpyDeviceToDevice, s));
+  launch_convert<double, float>((int64_t)gm.G * gm.Gq, h->Om64, h->Om32, 1.0, s);
+  // float32 copy used only by the inner solves of FP32_REFINE: Omega + s I
+  launch_shift_diag(gm.G, gm.Gq, h->Om64, h->Om32, h->opts.inner_shift, s);
+  GS_CUDA_TRY(cudaGetLastError());
+  h->has_w = false;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_set_opts(glm_sur_t h, const glm_sur_opts* opts) {
+  if (!h || !opts) return GLM_SUR_INVALID_ARG;
+  if (validate_opts(opts) != GLM_SUR_OK) return GLM_SUR_INVALID_ARG;
+  const bool need_q32 = opts->precision == GLM_SUR_PREC_FP32_REFINE && !h->Q32;
+  const bool prec_change = opts->precision != h->opts.precision || opts->stagnation_window != h->opts.stagnation_window;
+  h->opts = *opts;
+  if (need_q32) {
+    GS_CUDA_TRY(dalloc(&h->Q32, (size_t)h->gm.M * h->gm.np));
+    launch_convert<double, float>((int64_t)h->gm.M * h->gm.np, h->Q64, h->Q32, 1.0, nullptr);
+    GS_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (prec_change) free_workspace(h);
+  launch_convert<double, float>((int64_t)h->gm.G * h->gm.Gq, h->Om64, h->Om32, 1.0, nullptr);
+  launch_shift_diag(h->gm.G, h->gm.Gq, h->Om64, h->Om32, h->opts.inner_shift, nullptr);
+  GS_CUDA_TRY(cudaDeviceSynchronize());
+  h->plan_k = -1;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
+                             double* relres, glm_sur_stream_t stream) {
+  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G;
+  if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  glm_sur_status rc = ensure_workspace(h, k);
+  if (rc != GLM_SUR_OK) return rc;
+  const bool fp64 = h->opts.precision == GLM_SUR_PREC_FP64;
+  IterPlan p64;
+  rc = make_plan(h, k, true, p64);
+  if (rc != GLM_SUR_OK) return rc;
+  if (h->plan_k != k || h->plan_prec != h->opts.precision) {
+    IterPlan pit;
+    rc = make_plan(h, k, fp64, pit);
+    if (rc != GLM_SUR_OK) return rc;
+    h->plan = pit;
+    h->plan_k = k;
+    h->plan_prec = h->opts.precision;
+    h->graph.reset();
+  }
+  const int64_t mk = m * k;
+  const int maxit = h->opts.maxit > 0 ? h->opts.maxit : (int)std::min<int64_t>(m - gm.n + 1, 1 << 30);
+  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
+  h->launches += 1;
+  GS_CUDA_TRY(cudaGetLastError());
+  h->last_k = k;
+  if (fp64) {
+    rc = reset_state(h, k, h->opts.tol, maxit, h->opts.stagnation_window, s);
+    if (rc != GLM_SUR_OK) return rc;
+    rc = pcg_init<double>(h, k, h->y64, s);
+    if (rc != GLM_SUR_OK) return rc;
+    GS_CUDA_TRY(cudaGetLastError());
+    rc = run_steps<double>(h, k, maxit, s);
+    if (rc != GLM_SUR_OK) return rc;
+    GS_CUDA_TRY(cudaMemcpyAsync(h->d_status_final, h->st.status, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    GS_CUDA_TRY(cudaMemcpyAsync(h->d_iters_acc, h->st.iters, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    if (relres) GS_CUDA_TRY(cudaMemcpyAsync(relres, h->st.relres, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    // float64 iterative refinement on P Sigma w = P y (w in null(X^T)) with
+    // float32 inner PCG.  A correction that increases a column's float64
+    // residual is taken back and the column stops (its best w is kept).
+    GS_CUDA_TRY(cudaMemsetAsync(h->w64, 0, mk * sizeof(double), s));
+    GS_CUDA_TRY(cudaMemsetAsync(h->d_iters_acc, 0, k * sizeof(int), s));
+    std::vector<double> rho0(k, 0.0), prev(k, 0.0), cur(k, 0.0), rr_out(k, 0.0);
+    std::vector<int> fin(k, kStatusRunning), mask(2 * k, 0);
+    for (int outer = 0;; ++outer) {
+      rc = true_residual(h, k, p64, s);
+      if (rc != GLM_SUR_OK) return rc;
+      launch_sum_partials_sqrt(p64.n_update, k, h->cpart, h->norms, s);
+      h->launches += 1;
+      GS_CUDA_TRY(cudaMemcpyAsync(h->h_norms, h->norms, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      GS_CUDA_TRY(cudaStreamSynchronize(s));
+      bool all_done = true, any_revert = false;
+      for (int j = 0; j < k; ++j) {
+        cur[j] = h->h_norms[j];
+        if (outer == 0) rho0[j] = cur[j];
+        mask[k + j] = 0;
+        if (fin[j] == kStatusRunning) {
+          const double rr = rho0[j] > 0 ? cur[j] / rho0[j] : 0.0;
+          if (!std::isfinite(cur[j])) {
+            fin[j] = GLM_SUR_NONFINITE;
+          } else if (outer > 0 && cur[j] >= prev[j]) {
+            mask[k + j] = 1;            // take the last correction back
+            any_revert = true;
+            fin[j] = (rr_out[j] <= h->opts.tol) ? GLM_SUR_OK : GLM_SUR_STAGNATED;
+          } else {
+            rr_out[j] = rr;
+            prev[j] = cur[j];
+            if (rr <= h->opts.tol) fin[j] = GLM_SUR_OK;
+            else if (outer >= h->opts.max_refine) fin[j] = GLM_SUR_NOT_CONVERGED;
+          }
+        }
+        mask[j] = fin[j] == kStatusRunning;
+        if (mask[j]) all_done = false;
+      }
+      GS_CUDA_TRY(cudaMemcpyAsync(h->d_mask, mask.data(), 2 * k * sizeof(int), cudaMemcpyHostToDevice, s));
+      if (any_revert) {
+        launch_masked_axpy(mk, k, h->d_mask + k, -1.0, h->d64, h->w64, s);
+        h->launches += 1;
+      }
+      // (the host vector `mask` must outlive the copy above)
+      GS_CUDA_TRY(cudaStreamSynchronize(s));
+      if (all_done) break;
+      // inner float32 PCG on P Sigma_e d = rho (live columns)
+      rc = reset_state(h, k, h->opts.inner_tol, maxit, kInnerStagnation, s);
+      if (rc != GLM_SUR_OK) return rc;
+      launch_init_inner(h->plan, gm, k, h->g64, h->d_mask, h->g32, h->u32, h->w32, h->cpart, s);
+      h->launches += 1;
+      GS_CUDA_TRY(cudaGetLastError());
+      rc = run_steps<float>(h, k, maxit, s);
+      if (rc != GLM_SUR_OK) return rc;
+      // d = P (double) w32; w64 += d on the live columns.  The float32
+      // iterates leave null(X^T) by rounding while the solution w of
+      // eq. (aug1) lies in it (X^T w = 0), so the correction is projected
+      // in float64 before it is added.
+      rc = project_correction(h, k, p64, s);
+      if (rc != GLM_SUR_OK) return rc;
+      launch_add_int(k, h->st.iters, h->d_iters_acc, s);
+      h->launches += 1;
+      GS_CUDA_TRY(cudaGetLastError());
+    }
+    for (int j = 0; j < k; ++j) {
+      h->h_status[j] = fin[j];
+      h->h_norms[kMaxRhs + j] = rr_out[j];
+    }
+    GS_CUDA_TRY(cudaMemcpyAsync(h->d_status_final, h->h_status, k * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (relres)
+      GS_CUDA_TRY(cudaMemcpyAsync(relres, h->h_norms + kMaxRhs, k * sizeof(double), cudaMemcpyHostToDevice, s));
+    GS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, h->d_iters_acc, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  rc = recover_b(h, k, p64, b, ldb, s);
+  if (rc != GLM_SUR_OK) return rc;
+  h->has_w = true;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
+  if (!h || !status || k < 1 || k > h->last_k) return GLM_SUR_INVALID_ARG;
+  GS_CUDA_TRY(cudaDeviceSynchronize());
+  GS_CUDA_TRY(cudaMemcpy(status, h->d_status_final, k * sizeof(int), cudaMemcpyDeviceToHost));
+  glm_sur_status worst = GLM_SUR_OK;
+  for (int j = 0; j < k; ++j) {
+    if (status[j] == kStatusRunning) status[j] = GLM_SUR_NOT_CONVERGED;
+    if (status[j] != GLM_SUR_OK && worst == GLM_SUR_OK) worst = (glm_sur_status)status[j];
+  }
+  return worst;
+}
+
+glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream) {
+  if (!h || !w || !h->has_w || ldw < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_layout_to_colmajor<double>(h->gm, h->last_k, h->w64, w, ldw, s);
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* R, glm_sur_stream_t stream) {
+  if (!h || (Q && ldq < h->gm.M)) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const Geom& gm = h->gm;
+  if (Q) {
+    // padded row-major M x np  ->  column-major M x n
+    launch_unpad_q(gm, h->Q64, Q, ldq, s);
+    GS_CUDA_TRY(cudaGetLastError());
+  }
+  if (R) {
+    int64_t relems = 0;
+    for (int i = 0; i < gm.G; ++i) relems += (int64_t)h->n_i[i] * h->n_i[i];
+    GS_CUDA_TRY(cudaMemcpyAsync(R, h->R, relems * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  return GLM_SUR_OK;
+}
+
+int64_t glm_sur_launch_count(glm_sur_t h) { return h ? h->launches : -1; }
+
+glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_stream_t stream) {
+  if (!h || !ms || reps < 1 || h->last_k < 1 || h->plan_k != h->last_k) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int k = h->last_k;
+  const bool fp64 = h->opts.precision == GLM_SUR_PREC_FP64;
+  glm_sur_status rc = reset_state(h, k, 0.0, 1 << 30, 0, s);   // no stop tests
+  if (rc != GLM_SUR_OK) return rc;
+  if (fp64) rc = pcg_init<double>(h, k, h->y64, s);
+  else launch_init_inner(h->plan, h->gm, k, h->y64, nullptr, h->g32, h->u32, h->w32, h->cpart, s);
+  cudaEvent_t ev[5];
+  for (auto& e : ev) cudaEventCreate(&e);
+  double acc[5] = {0, 0, 0, 0, 0};
+  const IterPlan& p = h->plan;
+  auto one = [&](bool timed) {
+    if (timed) cudaEventRecord(ev[0], s);
+    if (fp64) {
+      double* Cp = reinterpret_cast<double*>(h->Cpart);
+      double* C = reinterpret_cast<double*>(h->Cfin);
+      launch_sigma_step<double>(p, h->gm, k, h->Om64, h->g64, h->u64, h->w64, h->S64, h->st, h->cpart, h->dpart, s);
+      if (timed) cudaEventRecord(ev[1], s);
+      launch_proj_partial<double>(p, h->gm, k, h->Q64, h->S64, Cp, h->st, 1, s);
+      if (timed) cudaEventRecord(ev[2], s);
+      launch_reduce<double>(p, h->gm, k, Cp, C, h->st, 1, h->dpart, s);
+      if (timed) cudaEventRecord(ev[3], s);
+      launch_proj_update<double>(p, h->gm, k, h->Q64, h->S64, h->g64, C, 1, h->st.lam, 0.0, h->cpart, h->st, 1, s);
+    } else {
+      float* Cp = reinterpret_cast<float*>(h->Cpart);
+      float* C = reinterpret_cast<float*>(h->Cfin);
+      launch_sigma_step<float>(p, h->gm, k, h->Om32, h->g32, h->u32, h->w32, h->S32, h->st, h->cpart, h->dpart, s);
+      if (timed) cudaEventRecord(ev[1], s);
+      launch_proj_partial<float>(p, h->gm, k, h->Q32, h->S32, Cp, h->st, 1, s);
+      if (timed) cudaEventRecord(ev[2], s);
+      launch_reduce<float>(p, h->gm, k, Cp, C, h->st, 1, h->dpart, s);
+      if (timed) cudaEventRecord(ev[3], s);
+      launch_proj_update<float>(p, h->gm, k, h->Q32, h->S32, h->g32, C, 1, h->st.lam, 0.0, h->cpart, h->st, 1, s);
+    }
+    if (timed) cudaEventRecord(ev[4], s);
+    h->launches += 4;
+  };
+  for (int r = 0; r < 3; ++r) one(false);
+  for (int r = 0; r < reps; ++r) {
+    one(true);
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) {
+      set_last_error(e, "profile step", __FILE__, __LINE__);
+      rc = GLM_SUR_CUDA_ERROR;
+      break;
+    }
+    float t;
+    for (int q = 0; q < 4; ++q) {
+      cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+      acc[q] += t;
+    }
+    cudaEventElapsedTime(&t, ev[0], ev[4]);
+    acc[4] += t;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (int q = 0; q < 5; ++q) ms[q] = acc[q] / reps;
+  h->has_w = false;
+  h->graph.reset();   // the captured graph baked the previous tolerance
+  return rc;
+}
+
+void glm_sur_destroy(glm_sur_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_workspace(h);
+  dfree(h->Q64); dfree(h->Q32); dfree(h->R); dfree(h->Om64); dfree(h->Om32); dfree(h->setup_flags);
+  dfree(h->gm.d_n_i); dfree(h->gm.d_off); dfree(h->gm.d_poff); dfree(h->gm.d_quad_blk); dfree(h->gm.d_r_off);
+  if (h->h_done) cudaFreeHost(h->h_done);
+  if (h->h_norms) cudaFreeHost(h->h_norms);
+  if (h->ev[0]) cudaEventDestroy(h->ev[0]);
+  if (h->ev[1]) cudaEventDestroy(h->ev[1]);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,808 @@
+// PCG-Aug iteration kernels for the SUR model (Algorithm glmpcg2 with D = I,
+// Sec. 5.3).  With D = I the preconditioner block Pi = (+)_i (I - Q_i Q_i^T)
+// =: P is an orthogonal projector, so the iteration keeps g = P r
+// (c = r^T Pi r = g^T g) and, because P X v = 0, updates it by
+// g <- g - lambda P (Sigma u): the X v term of step 7 never has to be formed.
+//
+// One step i of the iteration is four launches (all stream-ordered):
+//   sigma_step     : c_i from the partial sums of the previous step, the stop
+//                    tests and mu_{i-1} = c_i / c_{i-1} (every CTA computes the
+//                    same values); the lagged w_i = w_{i-1} - lambda_{i-1} u_{i-1};
+//                    u_i = g_i + mu_{i-1} u_{i-1}; S = U Omega (Sigma u, Sec. 5.3);
+//                    partial sums of d_i = u_i^T S (step 5).
+//   proj_partial   : partial sums over row ranges of C_i = Q_i^T S_i (X*^T-like
+//                    apply of Sec. 5.3 without the R^-1).
+//   reduce         : C = sum of partials (fixed order); lambda_i = c_i / d_i
+//                    (step 6) and the breakdown test d_i <= 0.
+//   proj_update    : t = S - Q C (= P Sigma u), g_{i+1} = g_i - lambda_i t
+//                    (steps 7-8), partial sums of c_{i+1} = g^T g.
+// Vectors are (M, G, k) row-major so that one row tile holds every block and
+// every right-hand side of a set of observations.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "pcg.h"
+
+namespace glmsur {
+
+// ---------------------------------------------------------------------------
+// per-column scalar logic of the step prologue (identical in every CTA)
+// ---------------------------------------------------------------------------
+struct StepScalars {
+  double mu;
+  double lam_prev;
+  int act;
+  int act_prev;
+};
+
+__device__ StepScalars step_prologue(const PcgState& st, int j, int k, const double* __restrict__ cpart,
+                                     int ncpart, bool writer) {
+  StepScalars out{};
+  const int it = *st.it;
+  double csum = 0.0;
+  for (int p = 0; p < ncpart; ++p) csum += cpart[(int64_t)p * k + j];
+  out.lam_prev = st.lam[j];
+  if (it == 0) {
+    const bool act = (csum > 0.0) && isfinite(csum);
+    out.act = act;
+    out.act_prev = 1;
+    out.mu = 0.0;
+    if (writer) {
+      st.c1[j] = csum;
+      st.c[0][j] = csum;
+      st.active[0][j] = act;
+      st.cbest[0][j] = csum;
+      st.itbest[0][j] = 0;
+      st.relres[j] = act ? 1.0 : 0.0;
+      st.status[j] = act ? kStatusRunning : (isfinite(csum) ? GLM_SUR_OK : GLM_SUR_NONFINITE);
+      st.iters[j] = 0;
+    }
+    return out;
+  }
+  const int sp = (it - 1) & 1, sc = it & 1;
+  const int ap = st.active[sp][j];
+  const double cp = st.c[sp][j];
+  out.act_prev = ap;
+  double cb = st.cbest[sp][j];
+  int ib = st.itbest[sp][j];
+  if (!ap) {
+    out.act = 0;
+    out.mu = 0.0;
+    if (writer) { st.c[sc][j] = cp; st.active[sc][j] = 0; st.cbest[sc][j] = cb; st.itbest[sc][j] = ib; }
+    return out;
+  }
+  const double c1 = st.c1[j];
+  const double rr = sqrt(fmax(csum, 0.0) / c1);
+  int act = 1, status = kStatusRunning;
+  if (csum < cb) { cb = csum; ib = it; }
+  // stop tests: breakdown, convergence, stagnation (no new minimum of c for
+  // W steps: c need not decrease monotonically), iteration cap
+  if (!isfinite(csum) || csum < 0.0) { act = 0; status = GLM_SUR_BREAKDOWN; }
+  else if (rr <= st.tol) { act = 0; status = GLM_SUR_OK; }
+  else if (st.W > 0 && it - ib >= st.W) { act = 0; status = GLM_SUR_STAGNATED; }
+  else if (it >= st.maxit) { act = 0; status = GLM_SUR_NOT_CONVERGED; }
+  out.act = act;
+  out.mu = act ? csum / cp : 0.0;
+  if (writer) {
+    st.c[sc][j] = act ? csum : cp;
+    st.active[sc][j] = act;
+    st.cbest[sc][j] = cb;
+    st.itbest[sc][j] = ib;
+    st.relres[j] = rr;
+    st.iters[j] = it;
+    if (!act) st.status[j] = status;
+  }
+  return out;
+}
+
+// Deterministic CTA reduction of per-thread partial sums, one per column
+// jj < JJ, where thread t holds column (t % JJ).  Result valid in threads
+// tid < JJ.  `red` needs (blockDim/32) * JJ doubles.
+template <int JJ>
+__device__ double reduce_cols_strided(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off >= JJ; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane < JJ) red[warp * JJ + lane] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < JJ)
+    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
+  return s;
+}
+
+// Every thread holds JJ partial sums (one per column); result in tid < JJ.
+template <int JJ>
+__device__ double reduce_cols_all(const double (&v)[JJ], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < JJ; ++jj) {
+    const double s = warp_sum(v[jj]);
+    if (lane == 0) red[warp * JJ + jj] = s;
+  }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < JJ)
+    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// sigma_step: prologue, lagged w update, u update, S = U Omega, d partials.
+// grid (nrowcta, 1, k / JJ); dynamic smem: Omega (G x Gq) + U tile (TR x G x JJ)
+// ---------------------------------------------------------------------------
+template <typename T, int JJ>
+__global__ void __launch_bounds__(256)
+k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, T* g, T* u, T* w, T* S,
+             PcgState st, const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Om_s = reinterpret_cast<T*>(smraw);
+  T* U_s = Om_s + (int64_t)G * Gq;
+  __shared__ double red[8 * 16];
+  __shared__ double mu_s[JJ], lamp_s[JJ];
+  __shared__ int act_s[JJ], anyp_s;
+  const int jg = blockIdx.z;
+  if (threadIdx.x == 0) anyp_s = 0;
+  __syncthreads();
+  if (threadIdx.x < JJ) {
+    const int j = jg * JJ + threadIdx.x;
+    const StepScalars sc = step_prologue(st, j, k, cpart, ncpart, blockIdx.x == 0);
+    mu_s[threadIdx.x] = sc.mu;
+    lamp_s[threadIdx.x] = sc.lam_prev;
+    act_s[threadIdx.x] = sc.act;
+    if (sc.act_prev) atomicOr(&anyp_s, 1);
+  }
+  __syncthreads();
+  if (!anyp_s) return;   // every column of this group already stopped: nothing changes
+  for (int64_t e = threadIdx.x; e < (int64_t)G * Gq; e += blockDim.x) Om_s[e] = Om[e];
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int nhq = Gq >> 2;
+  const int jj_t = threadIdx.x % JJ;
+  double dsum = 0.0;
+  __syncthreads();
+  for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+    const int tr = (int)((r1 - t0) < (int64_t)TR ? (r1 - t0) : (int64_t)TR);
+    // elementwise: w -= lam_prev u_old ; u = g + mu u_old (live columns)
+    const int ne = tr * G * JJ;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int jj = e % JJ, rest = e / JJ;
+      const int i = rest % G, t = rest / G;
+      const int64_t gi = ((t0 + t) * G + i) * k + jg * JJ + jj;
+      // arithmetic in T: the float32 bulk path issues no float64 instruction
+      // per element (float64 throughput is 1/58 of float32 on this part)
+      const T uo = u[gi];
+      const T lp = (T)lamp_s[jj];
+      if (lp != (T)0) w[gi] = w[gi] - lp * uo;
+      T un = uo;
+      if (act_s[jj]) {
+        un = g[gi] + (T)mu_s[jj] * uo;
+        u[gi] = un;
+      }
+      U_s[e] = un;
+    }
+    __syncthreads();
+    // S = U Omega on the tile; thread item (t, hq, jj) with jj = tid % JJ
+    const int nitems = tr * nhq * JJ;
+    T dloc = 0;
+    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+      const int rest = it / JJ;
+      const int hq = rest % nhq, t = rest / nhq;
+      T acc[4] = {0, 0, 0, 0};
+      const T* urow = U_s + (int64_t)t * G * JJ + jj_t;
+      for (int gg = 0; gg < G; ++gg) {
+        T om[4];
+        Vec4<T>::load(Om_s + (int64_t)gg * Gq + 4 * hq, om);
+        const T uv = urow[gg * JJ];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += uv * om[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int h = 4 * hq + c;
+        if (h < G) {
+          S[((t0 + t) * G + h) * k + jg * JJ + jj_t] = acc[c];
+          dloc += acc[c] * urow[h * JJ];
+        }
+      }
+    }
+    dsum += (double)dloc;
+    __syncthreads();
+  }
+  const double d = reduce_cols_strided<JJ>(dsum, red);
+  if (threadIdx.x < JJ) dpart[(int64_t)blockIdx.x * k + jg * JJ + threadIdx.x] = d;
+}
+
+// ---------------------------------------------------------------------------
+// sigma_resid: E = Y - W Omega  (no state; used for b = X*^T (y - Sigma w))
+// ---------------------------------------------------------------------------
+template <typename T, int JJ>
+__global__ void __launch_bounds__(256)
+k_sigma_resid(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ Y,
+              const T* __restrict__ Wv, T* E) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Om_s = reinterpret_cast<T*>(smraw);
+  T* U_s = Om_s + (int64_t)G * Gq;
+  const int jg = blockIdx.z;
+  for (int64_t e = threadIdx.x; e < (int64_t)G * Gq; e += blockDim.x) Om_s[e] = Om[e];
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int nhq = Gq >> 2;
+  const int jj_t = threadIdx.x % JJ;
+  __syncthreads();
+  for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+    const int tr = (int)((r1 - t0) < (int64_t)TR ? (r1 - t0) : (int64_t)TR);
+    const int ne = tr * G * JJ;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int jj = e % JJ, rest = e / JJ;
+      const int i = rest % G, t = rest / G;
+      U_s[e] = Wv[((t0 + t) * G + i) * k + jg * JJ + jj];
+    }
+    __syncthreads();
+    const int nitems = tr * nhq * JJ;
+    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+      const int rest = it / JJ;
+      const int hq = rest % nhq, t = rest / nhq;
+      T acc[4] = {0, 0, 0, 0};
+      const T* urow = U_s + (int64_t)t * G * JJ + jj_t;
+      for (int gg = 0; gg < G; ++gg) {
+        T om[4];
+        Vec4<T>::load(Om_s + (int64_t)gg * Gq + 4 * hq, om);
+        const T uv = urow[gg * JJ];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += uv * om[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int h = 4 * hq + c;
+        if (h < G) {
+          const int64_t gi = ((t0 + t) * G + h) * k + jg * JJ + jj_t;
+          E[gi] = Y[gi] - acc[c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// proj_partial: Cpart[rb] = sum_{t in rows(rb)} Q[t, col] * S[t, blk(col), j]
+// grid (nrb, nqgroups, k / JJ); thread = one column quad of the group.
+// ---------------------------------------------------------------------------
+template <typename T, int JJ>
+__global__ void __launch_bounds__(256)
+k_proj_partial(int64_t M, int G, int np, int nq, int k, const T* __restrict__ Q, const T* __restrict__ S,
+               const int* __restrict__ quad_blk, T* __restrict__ Cpart, PcgState st, int use_state) {
+  const int jg = blockIdx.z;
+  if (use_state) {
+    const int slot = (*st.it) & 1;
+    int any = 0;
+    for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jg * JJ + jj];
+    if (!any) return;
+  }
+  const int qpg = (int)ceil_div(nq, gridDim.y);
+  const int q = blockIdx.y * qpg + threadIdx.x;
+  if (threadIdx.x >= qpg || q >= nq) return;
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int blk = quad_blk[q];
+  T acc[4][JJ];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) acc[c][jj] = 0;
+  const T* qp = Q + r0 * np + 4 * q;
+  const T* sp = S + (r0 * G + blk) * k + jg * JJ;
+  const int64_t sstride = (int64_t)G * k;
+#pragma unroll 2
+  for (int64_t t = r0; t < r1; ++t) {
+    T qv[4];
+    Vec4<T>::load(qp, qv);
+    T sv[JJ];
+    if constexpr (JJ >= 4) {
+#pragma unroll
+      for (int a = 0; a < JJ / 4; ++a) {
+        T tmp[4];
+        Vec4<T>::load(sp + 4 * a, tmp);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) sv[4 * a + b] = tmp[b];
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) sv[jj] = sp[jj];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) acc[c][jj] += qv[c] * sv[jj];
+    qp += np;
+    sp += sstride;
+  }
+  T* dst = Cpart + ((int64_t)blockIdx.x * np + 4 * q) * k + jg * JJ;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) dst[(int64_t)c * k + jj] = acc[c][jj];
+}
+
+// ---------------------------------------------------------------------------
+// reduce: C[idx] = sum_rb Cpart[rb][idx] (fixed order), and in the last CTA
+// the scalar step lambda_i = c_i / d_i with the breakdown test.
+// grid (ceil(np*k / 32) + (scalar ? 1 : 0)); block 256 = 8 slices x 32 lanes
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_reduce(int64_t nidx, int nrb, const T* __restrict__ Cpart, T* __restrict__ C, PcgState st, int scalar,
+         const double* __restrict__ dpart, int ndpart) {
+  __shared__ double part[8][33];
+  __shared__ int nact_s;
+  const int k = st.k;
+  if (scalar && blockIdx.x == gridDim.x - 1) {
+    // scalar step for all k columns
+    const int it = *st.it;
+    const int slot = it & 1;
+    if (threadIdx.x == 0) nact_s = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      double d = 0.0;
+      for (int p = 0; p < ndpart; ++p) d += dpart[(int64_t)p * k + j];
+      int act = st.active[slot][j];
+      double lam = 0.0;
+      if (act) {
+        if (!(d > 0.0) || !isfinite(d)) {
+          act = 0;
+          st.active[slot][j] = 0;
+          st.status[j] = GLM_SUR_BREAKDOWN;
+          st.iters[j] = it;
+        } else {
+          lam = st.c[slot][j] / d;
+        }
+      }
+      st.lam[j] = lam;
+      if (act) atomicAdd(&nact_s, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (nact_s == 0) *st.done = 1;
+      *st.it = it + 1;
+    }
+    return;
+  }
+  // (the reduction CTAs never read the step counter: the scalar CTA of this
+  // same launch advances it)
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (idx < nidx)
+    for (int r = sl; r < nrb; r += 8) s += (double)Cpart[(int64_t)r * nidx + idx];
+  part[sl][lane] = s;
+  __syncthreads();
+  if (sl == 0 && idx < nidx) {
+    double tot = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tot += part[q][lane];
+    C[idx] = (T)tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// proj_update: t = S - Q C;  g = alpha g - lam_j t;  partials of g^T g.
+// lam_j = lam[j] when lam != nullptr, else lam_const.
+// grid (nrb, 1, k / JJ); thread item = (row, block), block index fastest.
+// ---------------------------------------------------------------------------
+template <typename T, int JJ>
+__global__ void __launch_bounds__(256)
+k_proj_update(int64_t M, int G, int np, int k, const T* __restrict__ Q, const T* __restrict__ S, T* g,
+              const T* __restrict__ C, const int* __restrict__ n_i, const int* __restrict__ poff, int alpha,
+              const double* __restrict__ lam, double lam_const, double* __restrict__ cpart, PcgState st,
+              int use_state) {
+  __shared__ double red[8 * 16];
+  const int jg = blockIdx.z;
+  if (use_state) {
+    const int slot = (*st.it - 1) & 1;   // reduce has already advanced the counter
+    int any = 0;
+    for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jg * JJ + jj];
+    if (!any) {
+      if (threadIdx.x < JJ) cpart[(int64_t)blockIdx.x * k + jg * JJ + threadIdx.x] = 0.0;
+      return;
+    }
+  }
+  T lam_r[JJ];
+#pragma unroll
+  for (int jj = 0; jj < JJ; ++jj) lam_r[jj] = (T)(lam ? lam[jg * JJ + jj] : lam_const);
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int64_t nitems = (r1 - r0) * G;
+  T cs[JJ];
+#pragma unroll
+  for (int jj = 0; jj < JJ; ++jj) cs[jj] = 0;
+  for (int64_t it = threadIdx.x; it < nitems; it += blockDim.x) {
+    const int i = (int)(it % G);
+    const int64_t t = r0 + it / G;
+    const int64_t base = (t * G + i) * k + jg * JJ;
+    T acc[JJ];
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) acc[jj] = S[base + jj];
+    const int nqi = (n_i[i] + 3) >> 2;
+    const int pc = poff[i];
+    const T* qrow = Q + t * np + pc;
+    for (int qq = 0; qq < nqi; ++qq) {
+      T qv[4];
+      Vec4<T>::load(qrow + 4 * qq, qv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const T* cr = C + (int64_t)(pc + 4 * qq + c) * k + jg * JJ;
+#pragma unroll
+        for (int jj = 0; jj < JJ; ++jj) acc[jj] -= qv[c] * __ldg(cr + jj);
+      }
+    }
+    T gl[JJ];
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) {
+      const T gold = alpha ? g[base + jj] : (T)0;
+      const T gn = gold - lam_r[jj] * acc[jj];
+      gl[jj] = gn;
+      cs[jj] += gn * gn;
+    }
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) g[base + jj] = gl[jj];
+  }
+  double csd[JJ];
+#pragma unroll
+  for (int jj = 0; jj < JJ; ++jj) csd[jj] = (double)cs[jj];
+  const double s = reduce_cols_all<JJ>(csd, red);
+  if (threadIdx.x < JJ) cpart[(int64_t)blockIdx.x * k + jg * JJ + threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// layout conversions and small helpers
+// ---------------------------------------------------------------------------
+
+// out[(t*G + i)*k + j] = scale * Y[j*ldy + i*M + t]   (32 x 32 tiles over (t, c = i*k + j))
+template <typename Tout>
+__global__ void k_colmajor_to_layout(int64_t M, int G, int k, const double* __restrict__ Y, int64_t ldy,
+                                     Tout* __restrict__ out, double scale) {
+  __shared__ double tile[32][33];
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int64_t c0 = (int64_t)blockIdx.y * 32;
+  const int64_t ncol = (int64_t)G * k;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 rows of 32
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t c = c0 + r, t = t0 + tx;
+    double v = 0.0;
+    if (c < ncol && t < M) {
+      const int64_t i = c / k, j = c % k;
+      v = Y[j * ldy + i * M + t];
+    }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t t = t0 + r, c = c0 + tx;
+    if (t < M && c < ncol) out[t * ncol + c] = (Tout)(scale * tile[tx][r]);
+  }
+}
+
+// Y[j*ldy + i*M + t] = in[(t*G + i)*k + j]
+template <typename Tin>
+__global__ void k_layout_to_colmajor(int64_t M, int G, int k, const Tin* __restrict__ in, double* __restrict__ Y,
+                                     int64_t ldy) {
+  __shared__ double tile[32][33];
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int64_t c0 = (int64_t)blockIdx.y * 32;
+  const int64_t ncol = (int64_t)G * k;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t t = t0 + r, c = c0 + tx;
+    tile[r][tx] = (t < M && c < ncol) ? (double)in[t * ncol + c] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t c = c0 + r, t = t0 + tx;
+    if (c < ncol && t < M) {
+      const int64_t i = c / k, j = c % k;
+      Y[j * ldy + i * M + t] = tile[tx][r];
+    }
+  }
+}
+
+// b_i = R_i^-1 C_i  (back substitution; one thread per (block, column))
+__global__ void k_tri_solve(int G, int k, const double* __restrict__ R, const int64_t* __restrict__ r_off,
+                            const int* __restrict__ n_i, const int* __restrict__ off,
+                            const int* __restrict__ poff, const double* __restrict__ C, double* b, int64_t ldb) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= G * k) return;
+  const int i = id / k, j = id % k;
+  const int ni = n_i[i];
+  const double* Ri = R + r_off[i];
+  double x[kMaxBlockCols];
+  for (int r = ni - 1; r >= 0; --r) {
+    double s = C[(int64_t)(poff[i] + r) * k + j];
+    for (int c = r + 1; c < ni; ++c) s -= Ri[r * ni + c] * x[c];
+    x[r] = s / Ri[r * ni + r];
+  }
+  for (int r = 0; r < ni; ++r) b[(int64_t)j * ldb + off[i] + r] = x[r];
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out, double scale) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (Tout)(scale * (double)in[e]);
+}
+
+// w64 += d (refinement correction)
+template <typename Tin>
+__global__ void k_add_to_f64(int64_t n, const Tin* __restrict__ d, double* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    w[e] += (double)d[e];
+}
+
+// inner start of a refinement step: g32 = -(float)rho, u32 = w32 = 0, partials of g32^T g32
+__global__ void __launch_bounds__(256)
+k_init_inner(int64_t M, int Gk, int k, const double* __restrict__ rho, const int* __restrict__ live, float* g,
+             float* u, float* w, double* __restrict__ cpart) {
+  __shared__ double red[8 * kMaxRhs];
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int64_t e0 = r0 * Gk, e1 = r1 * Gk;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    g[e] = (live == nullptr || live[e % k]) ? (float)(-rho[e]) : 0.f;
+    u[e] = 0.f;
+    w[e] = 0.f;
+  }
+  __syncthreads();
+  // second pass for the per-column sums (k <= 64): warp w sums column j = w, w+8, ...
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < k; j += 8) {
+    double s = 0.0;
+    for (int64_t e = e0 + j + (int64_t)lane * k; e < e1; e += (int64_t)32 * k) {
+      const double v = (double)g[e];
+      s += v * v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) red[j] = s;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cpart[(int64_t)blockIdx.x * k + j] = red[j];
+}
+
+// per-column sums of squares of a (M, G, k) vector over row ranges (partials)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_colsumsq(int64_t M, int Gk, int k, const T* __restrict__ v, double* __restrict__ part) {
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int64_t e0 = r0 * Gk, e1 = r1 * Gk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < k; j += 8) {
+    double s = 0.0;
+    for (int64_t e = e0 + j + (int64_t)lane * k; e < e1; e += (int64_t)32 * k) {
+      const double x = (double)v[e];
+      s += x * x;
+    }
+    s = warp_sum(s);
+    if (lane == 0) part[(int64_t)blockIdx.x * k + j] = s;
+  }
+}
+
+// w[e] += sign * d[e] for the columns j = e % k with mask[j] != 0
+__global__ void k_masked_axpy(int64_t n, int k, const int* __restrict__ mask, double sign,
+                              const double* __restrict__ d, double* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    if (mask[e % k]) w[e] += sign * d[e];
+}
+
+// Om32[i][i] += rel * max_i Om64[i][i]   (one thread: G <= 1024)
+__global__ void k_shift_diag(int G, int Gq, const double* __restrict__ Om64, float* __restrict__ Om32, double rel) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || rel == 0.0) return;
+  double mx = 0.0;
+  for (int i = 0; i < G; ++i) mx = fmax(mx, Om64[(int64_t)i * Gq + i]);
+  const double sh = rel * mx;
+  for (int i = 0; i < G; ++i) Om32[(int64_t)i * Gq + i] = (float)(Om64[(int64_t)i * Gq + i] + sh);
+}
+
+__global__ void k_add_int(int n, const int* __restrict__ a, int* __restrict__ acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) acc[j] += a[j];
+}
+
+// finalize sums of partials: out[j] = sqrt(sum_p part[p*k+j])
+__global__ void k_sum_partials_sqrt(int np_, int k, const double* __restrict__ part, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int p = 0; p < np_; ++p) s += part[(int64_t)p * k + j];
+  out[j] = sqrt(s);
+}
+
+// Q_cm[c*ldq + t] = Q[t*np + poff(blk(c)) + c - off(blk(c))]   (padded row-major -> column-major)
+__global__ void k_unpad_q(int64_t M, int G, int np, const int* __restrict__ off, const int* __restrict__ poff,
+                          const double* __restrict__ Q, double* __restrict__ out, int64_t ldq) {
+  const int i = blockIdx.y;
+  const int ni = off[i + 1] - off[i];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M * ni; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e % M;
+    const int c = (int)(e / M);
+    out[(int64_t)(off[i] + c) * ldq + t] = Q[t * np + poff[i] + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T, int JJ>
+static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
+                                 const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
+  dim3 grid(p.n_sigma, 1, k / JJ);
+  const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
+  k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, st, cpart, p.n_update,
+                                              dpart);
+}
+
+template <typename T, int JJ>
+static void launch_sigma_resid_jj(const IterPlan& p, const Geom& gm, int k, const T* Om, const T* Y, const T* W,
+                                  T* E, cudaStream_t s) {
+  dim3 grid(p.n_sigma, 1, k / JJ);
+  const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
+  k_sigma_resid<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, Y, W, E);
+}
+
+template <typename T, int JJ>
+static void launch_proj_partial_jj(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* Cpart,
+                                   const PcgState& st, int use_state, cudaStream_t s) {
+  dim3 grid(p.n_partial_rows, p.n_qgroups, k / JJ);
+  const int qpg = (int)ceil_div(gm.nq, p.n_qgroups);
+  const int threads = (int)std::min<int64_t>(256, ceil_div(qpg, 32) * 32);
+  k_proj_partial<T, JJ><<<grid, threads, 0, s>>>(gm.M, gm.G, gm.np, gm.nq, k, Q, S, gm.d_quad_blk, Cpart, st,
+                                                 use_state);
+}
+
+template <typename T, int JJ>
+static void launch_proj_update_jj(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g,
+                                  const T* C, int alpha, const double* lam, double lam_const, double* cpart,
+                                  const PcgState& st, int use_state, cudaStream_t s) {
+  dim3 grid(p.n_update, 1, k / JJ);
+  k_proj_update<T, JJ><<<grid, 256, 0, s>>>(gm.M, gm.G, gm.np, k, Q, S, g, C, gm.d_n_i, gm.d_poff, alpha, lam,
+                                            lam_const, cpart, st, use_state);
+}
+
+#define GS_DISPATCH_JJ(JJv, CALL) \
+  switch (JJv) {                  \
+    case 16: CALL(16); break;     \
+    case 8: CALL(8); break;       \
+    case 4: CALL(4); break;       \
+    case 2: CALL(2); break;       \
+    default: CALL(1); break;      \
+  }
+
+template <typename T>
+void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
+                       const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
+#define C_(J) launch_sigma_step_jj<T, J>(p, gm, k, Om, g, u, w, S, st, cpart, dpart, s)
+  GS_DISPATCH_JJ(p.JJ, C_)
+#undef C_
+}
+template <typename T>
+void launch_sigma_resid(const IterPlan& p, const Geom& gm, int k, const T* Om, const T* Y, const T* W, T* E,
+                        cudaStream_t s) {
+#define C_(J) launch_sigma_resid_jj<T, J>(p, gm, k, Om, Y, W, E, s)
+  GS_DISPATCH_JJ(p.JJ, C_)
+#undef C_
+}
+template <typename T>
+void launch_proj_partial(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* Cpart,
+                         const PcgState& st, int use_state, cudaStream_t s) {
+#define C_(J) launch_proj_partial_jj<T, J>(p, gm, k, Q, S, Cpart, st, use_state, s)
+  GS_DISPATCH_JJ(p.JJ, C_)
+#undef C_
+}
+template <typename T>
+void launch_reduce(const IterPlan& p, const Geom& gm, int k, const T* Cpart, T* C, const PcgState& st, int scalar,
+                   const double* dpart, cudaStream_t s) {
+  const int64_t nidx = (int64_t)gm.np * k;
+  const int nblk = (int)ceil_div(nidx, 32) + (scalar ? 1 : 0);
+  k_reduce<T><<<nblk, 256, 0, s>>>(nidx, p.n_partial_rows, Cpart, C, st, scalar, dpart, p.n_sigma);
+}
+template <typename T>
+void launch_proj_update(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g, const T* C,
+                        int alpha, const double* lam, double lam_const, double* cpart, const PcgState& st,
+                        int use_state, cudaStream_t s) {
+#define C_(J) launch_proj_update_jj<T, J>(p, gm, k, Q, S, g, C, alpha, lam, lam_const, cpart, st, use_state, s)
+  GS_DISPATCH_JJ(p.JJ, C_)
+#undef C_
+}
+
+template <typename Tout>
+void launch_colmajor_to_layout(const Geom& gm, int k, const double* Y, int64_t ldy, Tout* out, double scale,
+                               cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(gm.M, 32), (unsigned)ceil_div((int64_t)gm.G * k, 32));
+  k_colmajor_to_layout<Tout><<<grid, 256, 0, s>>>(gm.M, gm.G, k, Y, ldy, out, scale);
+}
+template <typename Tin>
+void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(gm.M, 32), (unsigned)ceil_div((int64_t)gm.G * k, 32));
+  k_layout_to_colmajor<Tin><<<grid, 256, 0, s>>>(gm.M, gm.G, k, in, Y, ldy);
+}
+
+void launch_tri_solve(const Geom& gm, int k, const double* R, const double* C, double* b, int64_t ldb,
+                      cudaStream_t s) {
+  const int n = gm.G * k;
+  k_tri_solve<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(gm.G, k, R, gm.d_r_off, gm.d_n_i, gm.d_off, gm.d_poff, C,
+                                                        b, ldb);
+}
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin* in, Tout* out, double scale, cudaStream_t s) {
+  k_convert<Tin, Tout><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, s>>>(n, in, out, scale);
+}
+template <typename Tin>
+void launch_add_to_f64(int64_t n, const Tin* d, double* w, cudaStream_t s) {
+  k_add_to_f64<Tin><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, s>>>(n, d, w);
+}
+template void launch_add_to_f64<float>(int64_t, const float*, double*, cudaStream_t);
+template void launch_add_to_f64<double>(int64_t, const double*, double*, cudaStream_t);
+void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, float* g,
+                       float* u, float* w, double* cpart, cudaStream_t s) {
+  k_init_inner<<<p.n_update, 256, 0, s>>>(gm.M, gm.G * k, k, rho, live, g, u, w, cpart);
+}
+template <typename T>
+void launch_colsumsq(const IterPlan& p, const Geom& gm, int k, const T* v, double* part, cudaStream_t s) {
+  k_colsumsq<T><<<p.n_update, 256, 0, s>>>(gm.M, gm.G * k, k, v, part);
+}
+void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, cudaStream_t s) {
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(gm.M * 8, 256), 4096), gm.G);
+  k_unpad_q<<<grid, 256, 0, s>>>(gm.M, gm.G, gm.np, gm.d_off, gm.d_poff, Q, out, ldq);
+}
+void launch_masked_axpy(int64_t n, int k, const int* mask, double sign, const double* d, double* w,
+                        cudaStream_t s) {
+  k_masked_axpy<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, s>>>(n, k, mask, sign, d, w);
+}
+void launch_shift_diag(int G, int Gq, const double* Om64, float* Om32, double rel, cudaStream_t s) {
+  k_shift_diag<<<1, 32, 0, s>>>(G, Gq, Om64, Om32, rel);
+}
+void launch_add_int(int n, const int* a, int* acc, cudaStream_t s) {
+  k_add_int<<<(unsigned)ceil_div(n, 64), 64, 0, s>>>(n, a, acc);
+}
+void launch_sum_partials_sqrt(int np_, int k, const double* part, double* out, cudaStream_t s) {
+  k_sum_partials_sqrt<<<1, 64, 0, s>>>(np_, k, part, out);
+}
+
+template <typename T>
+cudaError_t set_smem_attrs(int JJ, size_t bytes) {
+  cudaError_t e = cudaSuccess;
+#define C_(J)                                                                                                    \
+  e = cudaFuncSetAttribute(k_sigma_step<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);        \
+  if (e == cudaSuccess)                                                                                          \
+    e = cudaFuncSetAttribute(k_sigma_resid<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  GS_DISPATCH_JJ(JJ, C_)
+#undef C_
+  return e;
+}
+
+// explicit instantiations
+template void launch_sigma_step<double>(const IterPlan&, const Geom&, int, const double*, double*, double*, double*,
+                                        double*, const PcgState&, const double*, double*, cudaStream_t);
+template void launch_sigma_step<float>(const IterPlan&, const Geom&, int, const float*, float*, float*, float*,
+                                       float*, const PcgState&, const double*, double*, cudaStream_t);
+template void launch_sigma_resid<double>(const IterPlan&, const Geom&, int, const double*, const double*,
+                                         const double*, double*, cudaStream_t);
+template void launch_proj_partial<double>(const IterPlan&, const Geom&, int, const double*, const double*, double*,
+                                          const PcgState&, int, cudaStream_t);
+template void launch_proj_partial<float>(const IterPlan&, const Geom&, int, const float*, const float*, float*,
+                                         const PcgState&, int, cudaStream_t);
+template void launch_reduce<double>(const IterPlan&, const Geom&, int, const double*, double*, const PcgState&, int,
+                                    const double*, cudaStream_t);
+template void launch_reduce<float>(const IterPlan&, const Geom&, int, const float*, float*, const PcgState&, int,
+                                   const double*, cudaStream_t);
+template void launch_proj_update<double>(const IterPlan&, const Geom&, int, const double*, const double*, double*,
+                                         const double*, int, const double*, double, double*, const PcgState&, int,
+                                         cudaStream_t);
+template void launch_proj_update<float>(const IterPlan&, const Geom&, int, const float*, const float*, float*,
+                                        const float*, int, const double*, double, double*, const PcgState&, int,
+                                        cudaStream_t);
+template void launch_colmajor_to_layout<double>(const Geom&, int, const double*, int64_t, double*, double,
+                                                cudaStream_t);
+template void launch_layout_to_colmajor<double>(const Geom&, int, const double*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, float>(int64_t, const double*, float*, double, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);
+template void launch_colsumsq<double>(const IterPlan&, const Geom&, int, const double*, double*, cudaStream_t);
+template cudaError_t set_smem_attrs<double>(int, size_t);
+template cudaError_t set_smem_attrs<float>(int, size_t);
+
+}  // namespace glmsur

@@ -1,0 +1,63 @@
+// Launch plans and host launchers of the PCG-Aug iteration kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace glmsur {
+
+// Grid shapes of one PCG configuration (fixed for a handle, k and precision).
+struct IterPlan {
+  int JJ = 1;              // right-hand sides per thread tile (divides k)
+  int TR = 1;              // rows per Sigma-apply tile
+  int n_sigma = 1;         // row CTAs of the Sigma-apply kernels (d partials)
+  int n_partial_rows = 1;  // row ranges of proj_partial (C partials)
+  int n_qgroups = 1;       // column-quad groups of proj_partial
+  int n_update = 1;        // row CTAs of proj_update (c partials)
+  size_t sigma_smem = 0;
+};
+
+template <typename T>
+void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
+                       const PcgState& st, const double* cpart, double* dpart, cudaStream_t s);
+template <typename T>
+void launch_sigma_resid(const IterPlan& p, const Geom& gm, int k, const T* Om, const T* Y, const T* W, T* E,
+                        cudaStream_t s);
+template <typename T>
+void launch_proj_partial(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* Cpart,
+                         const PcgState& st, int use_state, cudaStream_t s);
+template <typename T>
+void launch_reduce(const IterPlan& p, const Geom& gm, int k, const T* Cpart, T* C, const PcgState& st, int scalar,
+                   const double* dpart, cudaStream_t s);
+template <typename T>
+void launch_proj_update(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g, const T* C,
+                        int alpha, const double* lam, double lam_const, double* cpart, const PcgState& st,
+                        int use_state, cudaStream_t s);
+template <typename Tout>
+void launch_colmajor_to_layout(const Geom& gm, int k, const double* Y, int64_t ldy, Tout* out, double scale,
+                               cudaStream_t s);
+template <typename Tin>
+void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s);
+void launch_tri_solve(const Geom& gm, int k, const double* R, const double* C, double* b, int64_t ldb,
+                      cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin* in, Tout* out, double scale, cudaStream_t s);
+template <typename Tin>
+void launch_add_to_f64(int64_t n, const Tin* d, double* w, cudaStream_t s);
+void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, float* g,
+                       float* u, float* w, double* cpart, cudaStream_t s);
+void launch_masked_axpy(int64_t n, int k, const int* mask, double sign, const double* d, double* w,
+                        cudaStream_t s);
+template <typename T>
+void launch_colsumsq(const IterPlan& p, const Geom& gm, int k, const T* v, double* part, cudaStream_t s);
+void launch_sum_partials_sqrt(int np_, int k, const double* part, double* out, cudaStream_t s);
+void launch_add_int(int n, const int* a, int* acc, cudaStream_t s);
+void launch_shift_diag(int G, int Gq, const double* Om64, float* Om32, double rel, cudaStream_t s);
+void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, cudaStream_t s);
+template <typename T>
+cudaError_t set_smem_attrs(int JJ, size_t bytes);
+
+}  // namespace glmsur

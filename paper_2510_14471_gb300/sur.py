@@ -1,0 +1,118 @@
+"""PyTorch-facing wrapper of the C ABI: torch tensors hold device memory,
+the library does every step of the method."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+PRECISIONS = {"fp64": L.GLM_SUR_PREC_FP64, "fp32_refine": L.GLM_SUR_PREC_FP32_REFINE}
+
+
+def _dev_f64(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64)
+    return torch.as_tensor(x, dtype=torch.float64, device=device)
+
+
+@dataclass
+class SolveResult:
+    b: torch.Tensor          # (n, k) float64, device
+    iters: torch.Tensor      # (k,) int32, device
+    relres: torch.Tensor     # (k,) float64, device
+    status: list             # k glm_sur_status codes (host)
+
+
+class GlmSur:
+    """SUR model handle: X_i factored once (TSQR on the device), Omega kept
+    on the device; ``solve`` runs PCG-Aug for k right-hand sides."""
+
+    def __init__(self, X_blocks, Omega, precision: str = "fp64", tol: float = 1e-12, maxit: int = 0,
+                 stagnation_window: int = 10, inner_tol: float = 1e-5, max_refine: int = 8,
+                 chunk: int = 16, inner_shift: float = 1e-6, device="cuda"):
+        self.device = torch.device(device)
+        blocks = [_dev_f64(x, self.device) for x in X_blocks]
+        self.n_i = [int(x.shape[1]) for x in blocks]
+        self.M = int(blocks[0].shape[0])
+        self.G = len(blocks)
+        self.n = sum(self.n_i)
+        # [X_1 ... X_G] column-major (M x n, ld = M) == row-major (n, M)
+        self._X = torch.cat([x.t() for x in blocks], dim=0).contiguous()
+        self._Omega = _dev_f64(Omega, self.device).contiguous()
+        self.opts = L.default_opts()
+        self.opts.precision = PRECISIONS[precision]
+        self.opts.tol = tol
+        self.opts.maxit = maxit
+        self.opts.stagnation_window = stagnation_window
+        self.opts.inner_tol = inner_tol
+        self.opts.max_refine = max_refine
+        self.opts.chunk = chunk
+        self.opts.inner_shift = inner_shift
+        self._h = L.glm_sur_setup(self.G, self.M, self.n_i, self._X.data_ptr(), self.M, self._Omega.data_ptr(),
+                                  self.opts, self._stream())
+
+    @staticmethod
+    def _stream() -> int:
+        return torch.cuda.current_stream().cuda_stream
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def setup_status(self) -> int:
+        return L.glm_sur_get_setup_status(self._h)
+
+    def set_omega(self, Omega) -> None:
+        self._Omega = _dev_f64(Omega, self.device).contiguous()
+        L.glm_sur_set_omega(self._h, self._Omega.data_ptr(), self._stream())
+
+    def set_options(self, **kw) -> None:
+        for key, v in kw.items():
+            if key == "precision":
+                v = PRECISIONS[v]
+            setattr(self.opts, key, v)
+        L.glm_sur_set_opts(self._h, self.opts)
+
+    def solve(self, Y) -> SolveResult:
+        """Y: (m, k) (column j = vec(Y_j)) or (m,).  Returns b as (n, k)."""
+        Y = _dev_f64(Y, self.device)
+        if Y.dim() == 1:
+            Y = Y[:, None]
+        m, k = Y.shape
+        Ycm = Y.t().contiguous()                     # column-major m x k
+        b = torch.empty((k, self.n), dtype=torch.float64, device=self.device)
+        iters = torch.zeros(k, dtype=torch.int32, device=self.device)
+        relres = torch.zeros(k, dtype=torch.float64, device=self.device)
+        L.glm_sur_solve(self._h, Ycm.data_ptr(), m, k, b.data_ptr(), self.n, iters.data_ptr(), relres.data_ptr(),
+                        self._stream())
+        status = L.glm_sur_get_status(self._h, k)
+        return SolveResult(b.t(), iters, relres, status)
+
+    def w(self, k: int) -> torch.Tensor:
+        out = torch.empty((k, self.M * self.G), dtype=torch.float64, device=self.device)
+        L.glm_sur_get_w(self._h, out.data_ptr(), self.M * self.G, self._stream())
+        return out.t()
+
+    def factors(self):
+        """(Q (M, n) with Q_i side by side, [R_i] list of (n_i, n_i))."""
+        Q = torch.empty((self.n, self.M), dtype=torch.float64, device=self.device)
+        R = torch.empty(sum(v * v for v in self.n_i), dtype=torch.float64, device=self.device)
+        L.glm_sur_get_factors(self._h, Q.data_ptr(), self.M, R.data_ptr(), self._stream())
+        Rs, off = [], 0
+        for v in self.n_i:
+            Rs.append(R[off:off + v * v].view(v, v))
+            off += v * v
+        return Q.t(), Rs
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            L.glm_sur_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: the target accuracy of the method is a relative error
+||b - b_oracle|| / ||b_oracle|| <= 1e-9 per right-hand side (float64 PCG and
+float32-bulk + float64 refinement alike); QR factors are checked at the
+float64 rounding level of a Householder QR (Sec. 5.3 factorisation)."""
+import numpy as np
+import pytest
+
+from oracle import sur_oracle as O
+from synth import sur_inputs as S
+
+pytestmark = pytest.mark.gpu
+
+TOL_B = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_14471_gb300 import build
+    build.build()
+
+
+def _glmsur():
+    from paper_2510_14471_gb300.sur import GlmSur
+    return GlmSur
+
+
+def relcols(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return np.max(np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300))
+
+
+def gpu_solve(p, precision="fp64", **kw):
+    h = _glmsur()(p.X_blocks, p.Omega, precision=precision, **kw)
+    r = h.solve(p.Y)
+    out = dict(b=r.b.cpu().numpy(), iters=r.iters.cpu().numpy(), relres=r.relres.cpu().numpy(),
+               status=r.status, h=h)
+    return out
+
+
+# ------------------------------------------------------------------ setup QR
+
+@pytest.mark.parametrize("M,n_i", [(1000, [1, 5, 17, 32]), (5000, [4, 9]), (20011, [32, 8]), (700, [64, 40, 33]),
+                                   (37, [37, 3])])
+def test_tsqr_factors(M, n_i):
+    g = S.rng(100 + M)
+    X = S.gaussian_blocks(g, M, n_i, cond_max=1e3)
+    Om = np.eye(len(n_i))
+    h = _glmsur()(X, Om)
+    assert h.setup_status() == 0
+    Q, Rs = h.factors()
+    Q = Q.cpu().numpy()
+    off = 0
+    for i, Xi in enumerate(X):
+        ni = n_i[i]
+        Qi = Q[:, off:off + ni]
+        Ri = Rs[i].cpu().numpy()
+        assert np.allclose(np.tril(Ri, -1), 0.0)
+        assert np.linalg.norm(Qi.T @ Qi - np.eye(ni)) <= 1e-14 * ni * max(1.0, np.sqrt(M / 100))
+        assert np.linalg.norm(Qi @ Ri - Xi) / np.linalg.norm(Xi) <= 1e-14 * max(1.0, np.sqrt(M / 100))
+        # R is unique up to the signs of its rows
+        Rn = np.linalg.qr(Xi, mode="r")
+        D = np.sign(np.diag(Ri)) * np.sign(np.diag(Rn))
+        assert np.linalg.norm(D[:, None] * Ri - Rn) / np.linalg.norm(Rn) <= 1e-12
+        off += ni
+
+
+def test_rank_deficient_block_is_reported():
+    g = S.rng(7)
+    X = S.gaussian_blocks(g, 300, [4, 5])
+    X[1][:, 3] = X[1][:, 1]
+    h = _glmsur()(X, np.eye(2))
+    assert h.setup_status() == 2   # GLM_SUR_RANK_DEFICIENT
+
+
+# ------------------------------------------------------------------ float64 PCG
+
+def test_config0_fp64_matches_dense_and_reference_pcg():
+    p = S.config0()
+    _, b_dense = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
+    ref = O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=1e-12)
+    r = gpu_solve(p, tol=1e-12)
+    assert r["status"] == [0]
+    assert relcols(r["b"], b_dense) <= TOL_B
+    assert abs(int(r["iters"][0]) - int(ref["iters"][0])) <= 2
+
+
+@pytest.mark.parametrize("G,M,n_i,k,omega,rank", [
+    (3, 97, [2, 5, 3], 1, "chol", None),          # ragged, single tile
+    (4, 1037, [7, 1, 12, 4], 3, "spectrum", None),  # ragged tail, k not a power of two
+    (5, 2049, [8, 8, 3, 16, 5], 16, "wishart", None),
+    (6, 513, [3, 4, 2, 5, 3, 4], 2, "lowrank", 4),   # singular Omega
+    (9, 300, [2] * 9, 8, "diag", None),
+    (2, 64, [64, 1], 1, "chol", None),              # n_i = M for one block, widest block
+])
+def test_fp64_small_cases_match_oracle(G, M, n_i, k, omega, rank):
+    p = S.make_problem(G=G, M=M, n_i=n_i, k=k, seed=G * 1000 + M, omega=omega, rank=rank)
+    b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)
+    r = gpu_solve(p, tol=1e-12)
+    assert all(s in (0, 4) for s in r["status"]), r["status"]
+    assert relcols(r["b"], b_ref) <= TOL_B
+
+
+def test_iteration_counts_match_reference_pcg():
+    p = S.make_problem(G=6, M=400, n_i=[3, 5, 2, 7, 4, 6], k=4, seed=17, omega="chol")
+    ref = O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=1e-10)
+    r = gpu_solve(p, tol=1e-10)
+    assert np.all(np.abs(r["iters"].astype(int) - ref["iters"].astype(int)) <= 2), (r["iters"], ref["iters"])
+    assert relcols(r["b"], ref["b"]) <= TOL_B
+
+
+def test_omega_scaled_identity_takes_one_step():
+    p = S.make_problem(G=4, M=500, n_i=[3, 4, 5, 6], k=2, seed=3, omega="ident")
+    r = gpu_solve(p, tol=1e-12)
+    assert list(r["iters"]) == [1, 1]
+    assert relcols(r["b"], O.ols_blocks(p.X_blocks, p.Y)) <= 1e-12
+
+
+def test_square_blocks_need_no_iteration():
+    # M = n_i for every block: P = 0, so g_1 = -P y is zero up to rounding and
+    # at most one (rounding-sized) step is taken; b = X_i^-1 y_i
+    p = S.make_problem(G=3, M=6, n_i=[6, 6, 6], k=1, seed=4, omega="chol")
+    r = gpu_solve(p, tol=1e-12)
+    assert int(r["iters"][0]) <= 1
+    assert relcols(r["b"], O.ols_blocks(p.X_blocks, p.Y)) <= 1e-11
+
+
+def test_w_stays_in_null_space_of_Xt():
+    p = S.make_problem(G=4, M=800, n_i=[5, 6, 7, 8], k=2, seed=12, omega="spectrum")
+    r = gpu_solve(p, tol=1e-12)
+    w = r["h"].w(2).cpu().numpy()
+    top, bot = O.augmented_residual(p.X_blocks, p.Omega, p.Y, w, r["b"])
+    assert np.linalg.norm(bot) <= 1e-10 * np.linalg.norm(p.Y)
+    assert np.linalg.norm(top) <= 1e-8 * np.linalg.norm(p.Y)
+
+
+def test_set_omega_reuses_factors():
+    p = S.make_problem(G=4, M=600, n_i=[5, 6, 7, 8], k=1, seed=13, omega="chol")
+    q = S.make_problem(G=4, M=600, n_i=[5, 6, 7, 8], k=1, seed=13, omega="spectrum")
+    h = _glmsur()(p.X_blocks, p.Omega)
+    h.set_omega(q.Omega)
+    r = h.solve(p.Y)
+    b_ref = O.sur_gls_structured(p.X_blocks, q.Omega, p.Y)
+    assert relcols(r.b.cpu().numpy(), b_ref) <= TOL_B
+
+
+# ------------------------------------------------------------------ float32 bulk + float64 refinement
+
+@pytest.mark.parametrize("G,M,n_i,k,omega,rank", [
+    (3, 997, [2, 5, 3], 1, "chol", None),
+    (5, 2049, [8, 8, 3, 16, 5], 16, "wishart", None),
+    (6, 1513, [3, 4, 2, 5, 3, 4], 4, "lowrank", 4),
+])
+def test_fp32_refine_matches_oracle(G, M, n_i, k, omega, rank):
+    p = S.make_problem(G=G, M=M, n_i=n_i, k=k, seed=G * 7 + M, omega=omega, rank=rank)
+    b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)
+    r = gpu_solve(p, precision="fp32_refine", tol=1e-12)
+    assert all(s in (0, 4) for s in r["status"]), r["status"]
+    assert relcols(r["b"], b_ref) <= TOL_B
+
+
+# ------------------------------------------------------------------ singular Omega: exact recovery
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_singular_omega_recovers_beta_true(precision):
+    # Omega = A A^T of rank r < G with noise (A (x) I) z: b = beta_true exactly
+    p = S.config1(k=2, M=2000, G=16, rank=12)
+    r = gpu_solve(p, precision=precision, tol=1e-12)
+    assert relcols(r["b"], p.beta) <= TOL_B
