@@ -143,7 +143,7 @@ def oracle_iters_per_solve():
     path = os.path.join(ROOT, "tests", "golden", "cfg1_oracle_iterations.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return int(max(d["iters"])), "oracle float64 PCG to tol 1e-12 (tests/golden/cfg1_oracle_iterations.json)"
+        return int(max(d["iters"])), "oracle float64 PCG to tol 1e-13 (tests/golden/cfg1_oracle_iterations.json)"
     return None, None
 
 
@@ -194,7 +194,7 @@ def run_ours(args, rank, world, local, pg):
     # ---- setup (TSQR), timed separately
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = GlmSur(p.X_blocks, p.Omega, precision=args.precision, tol=1e-12, device=dev)
+    h = GlmSur(p.X_blocks, p.Omega, precision=args.precision, tol=1e-13, device=dev)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3   # includes the host->device copy of X
     Ycm = torch.as_tensor(p.Y.T.copy(), device=dev)                # column-major m x k
@@ -288,7 +288,7 @@ def run_ours(args, rank, world, local, pg):
     # ---- float64 PCG on the same workload (comparison at the same accuracy)
     fp64 = None
     if not args.no_fp64:
-        h64 = GlmSur(p.X_blocks, p.Omega, precision="fp64", tol=1e-12, device=dev)
+        h64 = GlmSur(p.X_blocks, p.Omega, precision="fp64", tol=1e-13, device=dev)
         Lh = h64.handle
         L.glm_sur_solve(Lh, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(), stream)
         torch.cuda.synchronize()
@@ -329,7 +329,7 @@ def run_ours(args, rank, world, local, pg):
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine" else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "G": G, "M": M, "n": n, "k": k, "precision": args.precision,
-                       "tol": 1e-12, "l2": "inputs larger than L2 (Q 205 MB f64 + 102 MB f32, vectors 82-164 MB)",
+                       "tol": 1e-13, "l2": "inputs larger than L2 (Q 205 MB f64 + 102 MB f32, vectors 82-164 MB)",
                        "parallelism": f"replicas{world}"},
             "per_rhs_solves_per_s": value * k,
             "rel_err_max": err, "status": status, "iters_max": int(it_used.max()),

@@ -65,7 +65,7 @@ typedef struct {
   int precision;          /* GLM_SUR_PREC_*                                         */
   double tol;             /* stop a column when sqrt(c_i / c_1) <= tol              */
   int maxit;              /* iteration cap of one PCG run (<= 0: m - n + 1)         */
-  int stagnation_window;  /* W: stagnated if c_i >= c_{i-W} (<= 0: 10)              */
+  int stagnation_window;  /* W: stagnated if c has no new minimum for W steps (0: off) */
   double inner_tol;       /* FP32_REFINE: relative reduction per inner solve        */
   int max_refine;         /* FP32_REFINE: cap on outer (refinement) steps           */
   int chunk;              /* iterations per captured CUDA graph launch (even, >= 2) */
@@ -74,8 +74,10 @@ typedef struct {
                              float64 residual always uses Omega itself        */
 } glm_sur_opts;
 
-/* Default options: FP64, tol 1e-12, maxit m-n+1, W = 10, inner_tol 1e-5,
- * max_refine 8, chunk 16, inner_shift 1e-6. */
+/* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
+ * max_refine 8, chunk 16, inner_shift 1e-6.  A column that stops without
+ * converging (stagnation, breakdown, maxit) returns its best saved iterate:
+ * w is saved whenever c falls below a quarter of the c of the previous save. */
 void glm_sur_default_opts(glm_sur_opts* opts);
 
 /*

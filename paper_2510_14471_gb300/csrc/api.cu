@@ -68,6 +68,8 @@ struct glm_sur_ctx {
   int kcap = 0;
   double *y64 = nullptr, *w64 = nullptr, *g64 = nullptr, *u64 = nullptr, *S64 = nullptr, *E64 = nullptr;
   float *g32 = nullptr, *u32 = nullptr, *w32 = nullptr, *S32 = nullptr;
+  double* wb64 = nullptr;       // best-iterate snapshots of w
+  float* wb32 = nullptr;
   double* d64 = nullptr;        // last projected refinement correction
   int* d_mask = nullptr;        // 2 x k column masks (live columns, columns to revert)
   void* Cpart = nullptr;
@@ -95,7 +97,7 @@ struct glm_sur_ctx {
 
 namespace {
 
-constexpr int kStateDoubles = 7;
+constexpr int kStateDoubles = 10;
 constexpr int kStateInts = 6;
 constexpr int kInnerStagnation = 25;   // stagnation window of the float32 inner solves
 
@@ -130,8 +132,16 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   p.n_sigma = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(gm.M, p.TR), ceil_div(target, njg)));
   p.n_qgroups = (int)std::max<int64_t>(1, ceil_div(gm.nq, 256));
   p.n_partial_rows = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, (int64_t)p.n_qgroups * njg)));
-  p.n_update = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, njg)));
-  cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem) : set_smem_attrs<float>(p.JJ, p.sigma_smem);
+  p.n_ugroups = gm.n_ugroups;
+  p.ug_max_quads = gm.ug_max_quads;
+  p.ug_threads = (int)std::min<int64_t>(512, ceil_div(gm.ug_max_quads, 32) * 32);
+  p.n_update = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, (int64_t)njg * p.n_ugroups)));
+  p.n_cpart = p.n_update * p.n_ugroups;
+  const size_t upd_row = sz * (size_t)gm.ug_max_quads * p.JJ;
+  p.TRB = (int)std::max<size_t>(2, std::min<size_t>(32, (48 * 1024) / upd_row));
+  p.update_smem = (size_t)p.TRB * upd_row;
+  cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem, p.update_smem)
+                            : set_smem_attrs<float>(p.JJ, p.sigma_smem, p.update_smem);
   if (e != cudaSuccess) {
     set_last_error(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
     return GLM_SUR_CUDA_ERROR;
@@ -141,7 +151,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
 
 void free_workspace(glm_sur_ctx* h) {
   dfree(h->y64); dfree(h->w64); dfree(h->g64); dfree(h->u64); dfree(h->S64); dfree(h->E64);
-  dfree(h->g32); dfree(h->u32); dfree(h->w32); dfree(h->S32);
+  dfree(h->g32); dfree(h->u32); dfree(h->w32); dfree(h->S32); dfree(h->wb64); dfree(h->wb32);
   if (h->Cpart) cudaFree(h->Cpart);
   if (h->Cfin) cudaFree(h->Cfin);
   h->Cpart = h->Cfin = nullptr;
@@ -159,7 +169,7 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   free_workspace(h);
   const Geom& gm = h->gm;
   const size_t mk = (size_t)gm.M * gm.G * k;
-  const int maxrows = 2 * h->sms;   // upper bound of every row-CTA count in make_plan
+  const int maxrows = 2 * h->sms + gm.n_ugroups + 8;   // upper bound of every partial count in make_plan
   const size_t cpart_n = (size_t)maxrows * gm.np * k;
   GS_CUDA_TRY(dalloc(&h->y64, mk));
   GS_CUDA_TRY(dalloc(&h->w64, mk));
@@ -168,11 +178,13 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   if (h->opts.precision == GLM_SUR_PREC_FP64) {
     GS_CUDA_TRY(dalloc(&h->u64, mk));
     GS_CUDA_TRY(dalloc(&h->S64, mk));
+    GS_CUDA_TRY(dalloc(&h->wb64, mk));
   } else {
     GS_CUDA_TRY(dalloc(&h->g32, mk));
     GS_CUDA_TRY(dalloc(&h->u32, mk));
     GS_CUDA_TRY(dalloc(&h->w32, mk));
     GS_CUDA_TRY(dalloc(&h->S32, mk));
+    GS_CUDA_TRY(dalloc(&h->wb32, mk));
   }
   GS_CUDA_TRY(cudaMalloc(&h->Cpart, cpart_n * sizeof(double)));
   GS_CUDA_TRY(cudaMalloc(&h->Cfin, (size_t)gm.np * k * sizeof(double)));
@@ -197,6 +209,9 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   st.relres = h->st_buf + 4 * k;
   st.cbest[0] = h->st_buf + 5 * k;
   st.cbest[1] = h->st_buf + 6 * k;
+  st.csnap[0] = h->st_buf + 7 * k;
+  st.csnap[1] = h->st_buf + 8 * k;
+  st.cstop = h->st_buf + 9 * k;
   st.active[0] = h->st_ibuf;
   st.active[1] = h->st_ibuf + k;
   st.iters = h->st_ibuf + 2 * k;
@@ -231,6 +246,7 @@ struct Bufs<double> {
   static double* S(glm_sur_ctx* h) { return h->S64; }
   static double* Q(glm_sur_ctx* h) { return h->Q64; }
   static double* Om(glm_sur_ctx* h) { return h->Om64; }
+  static double* wb(glm_sur_ctx* h) { return h->wb64; }
 };
 template <>
 struct Bufs<float> {
@@ -240,6 +256,7 @@ struct Bufs<float> {
   static float* S(glm_sur_ctx* h) { return h->S32; }
   static float* Q(glm_sur_ctx* h) { return h->Q32; }
   static float* Om(glm_sur_ctx* h) { return h->Om32; }
+  static float* wb(glm_sur_ctx* h) { return h->wb32; }
 };
 
 // Enqueue n PCG steps (four launches each).
@@ -250,7 +267,7 @@ void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
   T* C = reinterpret_cast<T*>(h->Cfin);
   for (int i = 0; i < n; ++i) {
     launch_sigma_step<T>(p, h->gm, k, Bufs<T>::Om(h), Bufs<T>::g(h), Bufs<T>::u(h), Bufs<T>::w(h), Bufs<T>::S(h),
-                         h->st, h->cpart, h->dpart, s);
+                         Bufs<T>::wb(h), h->st, h->cpart, h->dpart, s);
     launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Cpart, h->st, 1, s);
     launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
     launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Bufs<T>::g(h), C, 1, h->st.lam, 0.0,
@@ -291,6 +308,10 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
       if (h->h_done[(c - 1) & 1]) break;
     }
   }
+  // columns that stopped without converging keep their best saved w
+  launch_restore_best<T>(h->gm.M * h->gm.G * k, k, h->st, Bufs<T>::wb(h), Bufs<T>::w(h), s);
+  h->launches += 2;
+  GS_CUDA_TRY(cudaGetLastError());
   return GLM_SUR_OK;
 }
 
@@ -308,6 +329,7 @@ glm_sur_status pcg_init(glm_sur_ctx* h, int k, const T* y_layout, cudaStream_t s
   h->launches += 3;
   GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::u(h), 0, mk * sizeof(T), s));
   GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::w(h), 0, mk * sizeof(T), s));
+  GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::wb(h), 0, mk * sizeof(T), s));
   return GLM_SUR_OK;
 }
 
@@ -358,9 +380,9 @@ extern "C" {
 void glm_sur_default_opts(glm_sur_opts* o) {
   if (!o) return;
   o->precision = GLM_SUR_PREC_FP64;
-  o->tol = 1e-12;
+  o->tol = 1e-13;
   o->maxit = 0;
-  o->stagnation_window = 10;
+  o->stagnation_window = 25;
   o->inner_tol = 1e-5;
   o->max_refine = 8;
   o->chunk = 16;
@@ -424,6 +446,23 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   gm.n = h->off[G];
   gm.np = h->poff[G];
   gm.nq = gm.np / 4;
+  // block groups of the projection update (runs of whole blocks, <= kMaxGroupQuads quads)
+  std::vector<int> ug_blk0(1, 0);
+  {
+    int cur = 0;
+    for (int i = 0; i < G; ++i) {
+      const int qi = round_up4(n_i[i]) / 4;
+      if (cur > 0 && cur + qi > kMaxGroupQuads) {
+        ug_blk0.push_back(i);
+        gm.ug_max_quads = std::max(gm.ug_max_quads, cur);
+        cur = 0;
+      }
+      cur += qi;
+    }
+    gm.ug_max_quads = std::max(gm.ug_max_quads, cur);
+    ug_blk0.push_back(G);
+    gm.n_ugroups = (int)ug_blk0.size() - 1;
+  }
   glm_sur_status rc = GLM_SUR_OK;
   auto bail = [&](glm_sur_status r) {
     glm_sur_destroy(h);
@@ -447,6 +486,8 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   SETUP_TRY(dalloc(&gm.d_poff, G + 1));
   SETUP_TRY(dalloc(&gm.d_quad_blk, gm.nq));
   SETUP_TRY(dalloc(&gm.d_r_off, G + 1));
+  SETUP_TRY(dalloc(&gm.d_ug_blk0, gm.n_ugroups + 1));
+  SETUP_TRY(cudaMemcpyAsync(gm.d_ug_blk0, ug_blk0.data(), (gm.n_ugroups + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   SETUP_TRY(cudaMemcpyAsync(gm.d_n_i, n_i, G * sizeof(int), cudaMemcpyHostToDevice, s));
   SETUP_TRY(cudaMemcpyAsync(gm.d_off, h->off.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   SETUP_TRY(cudaMemcpyAsync(gm.d_poff, h->poff.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -572,7 +613,7 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
     for (int outer = 0;; ++outer) {
       rc = true_residual(h, k, p64, s);
       if (rc != GLM_SUR_OK) return rc;
-      launch_sum_partials_sqrt(p64.n_update, k, h->cpart, h->norms, s);
+      launch_sum_partials_sqrt(p64.n_cpart, k, h->cpart, h->norms, s);
       h->launches += 1;
       GS_CUDA_TRY(cudaMemcpyAsync(h->h_norms, h->norms, k * sizeof(double), cudaMemcpyDeviceToHost, s));
       GS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -611,6 +652,7 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
       rc = reset_state(h, k, h->opts.inner_tol, maxit, kInnerStagnation, s);
       if (rc != GLM_SUR_OK) return rc;
       launch_init_inner(h->plan, gm, k, h->g64, h->d_mask, h->g32, h->u32, h->w32, h->cpart, s);
+      GS_CUDA_TRY(cudaMemsetAsync(h->wb32, 0, mk * sizeof(float), s));
       h->launches += 1;
       GS_CUDA_TRY(cudaGetLastError());
       rc = run_steps<float>(h, k, maxit, s);
@@ -698,7 +740,8 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
     if (fp64) {
       double* Cp = reinterpret_cast<double*>(h->Cpart);
       double* C = reinterpret_cast<double*>(h->Cfin);
-      launch_sigma_step<double>(p, h->gm, k, h->Om64, h->g64, h->u64, h->w64, h->S64, h->st, h->cpart, h->dpart, s);
+      launch_sigma_step<double>(p, h->gm, k, h->Om64, h->g64, h->u64, h->w64, h->S64, h->wb64, h->st, h->cpart,
+                                h->dpart, s);
       if (timed) cudaEventRecord(ev[1], s);
       launch_proj_partial<double>(p, h->gm, k, h->Q64, h->S64, Cp, h->st, 1, s);
       if (timed) cudaEventRecord(ev[2], s);
@@ -708,7 +751,8 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
     } else {
       float* Cp = reinterpret_cast<float*>(h->Cpart);
       float* C = reinterpret_cast<float*>(h->Cfin);
-      launch_sigma_step<float>(p, h->gm, k, h->Om32, h->g32, h->u32, h->w32, h->S32, h->st, h->cpart, h->dpart, s);
+      launch_sigma_step<float>(p, h->gm, k, h->Om32, h->g32, h->u32, h->w32, h->S32, h->wb32, h->st, h->cpart,
+                               h->dpart, s);
       if (timed) cudaEventRecord(ev[1], s);
       launch_proj_partial<float>(p, h->gm, k, h->Q32, h->S32, Cp, h->st, 1, s);
       if (timed) cudaEventRecord(ev[2], s);
@@ -749,6 +793,7 @@ void glm_sur_destroy(glm_sur_t h) {
   free_workspace(h);
   dfree(h->Q64); dfree(h->Q32); dfree(h->R); dfree(h->Om64); dfree(h->Om32); dfree(h->setup_flags);
   dfree(h->gm.d_n_i); dfree(h->gm.d_off); dfree(h->gm.d_poff); dfree(h->gm.d_quad_blk); dfree(h->gm.d_r_off);
+  dfree(h->gm.d_ug_blk0);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);

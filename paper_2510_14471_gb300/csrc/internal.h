@@ -56,7 +56,13 @@ struct Geom {
   int* d_poff = nullptr;     // padded column offsets (G+1)
   int* d_quad_blk = nullptr; // block of every column quad (nq)
   int64_t* d_r_off = nullptr;
+  // block groups of the projection update: runs of whole blocks with at most
+  // kMaxGroupQuads column quads each; group g = blocks [ug_blk0[g], ug_blk0[g+1])
+  int n_ugroups = 1, ug_max_quads = 1;
+  int* d_ug_blk0 = nullptr;
 };
+
+constexpr int kMaxGroupQuads = 512;
 
 // Device state of one batch of k PCG columns (one solve).
 struct PcgState {
@@ -70,6 +76,8 @@ struct PcgState {
   double* lam = nullptr;
   double* cbest[2] = {nullptr, nullptr};  // running minimum of c (parity slots)
   int* itbest[2] = {nullptr, nullptr};     // step at which it was reached
+  double* csnap[2] = {nullptr, nullptr};   // c at the last saved w (best-iterate snapshot)
+  double* cstop = nullptr;                 // c when the column stopped
   int* iters = nullptr;
   int* status = nullptr;
   double* relres = nullptr;

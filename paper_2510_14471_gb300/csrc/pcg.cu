@@ -34,14 +34,12 @@ struct StepScalars {
   double lam_prev;
   int act;
   int act_prev;
+  int snap;   // save w of this step as the best iterate so far
 };
 
-__device__ StepScalars step_prologue(const PcgState& st, int j, int k, const double* __restrict__ cpart,
-                                     int ncpart, bool writer) {
+__device__ StepScalars step_prologue(const PcgState& st, int j, int k, double csum, bool writer) {
   StepScalars out{};
   const int it = *st.it;
-  double csum = 0.0;
-  for (int p = 0; p < ncpart; ++p) csum += cpart[(int64_t)p * k + j];
   out.lam_prev = st.lam[j];
   if (it == 0) {
     const bool act = (csum > 0.0) && isfinite(csum);
@@ -54,6 +52,8 @@ __device__ StepScalars step_prologue(const PcgState& st, int j, int k, const dou
       st.active[0][j] = act;
       st.cbest[0][j] = csum;
       st.itbest[0][j] = 0;
+      st.csnap[0][j] = csum;
+      st.cstop[j] = csum;
       st.relres[j] = act ? 1.0 : 0.0;
       st.status[j] = act ? kStatusRunning : (isfinite(csum) ? GLM_SUR_OK : GLM_SUR_NONFINITE);
       st.iters[j] = 0;
@@ -66,12 +66,19 @@ __device__ StepScalars step_prologue(const PcgState& st, int j, int k, const dou
   out.act_prev = ap;
   double cb = st.cbest[sp][j];
   int ib = st.itbest[sp][j];
+  const double cs_prev = st.csnap[sp][j];
   if (!ap) {
     out.act = 0;
     out.mu = 0.0;
-    if (writer) { st.c[sc][j] = cp; st.active[sc][j] = 0; st.cbest[sc][j] = cb; st.itbest[sc][j] = ib; }
+    if (writer) {
+      st.c[sc][j] = cp; st.active[sc][j] = 0; st.cbest[sc][j] = cb; st.itbest[sc][j] = ib;
+      st.csnap[sc][j] = cs_prev;
+    }
     return out;
   }
+  // the w formed in this step (lagged update) is saved when c dropped below
+  // a quarter of the c of the previous save
+  out.snap = isfinite(csum) && csum < 0.25 * cs_prev;
   const double c1 = st.c1[j];
   const double rr = sqrt(fmax(csum, 0.0) / c1);
   int act = 1, status = kStatusRunning;
@@ -89,6 +96,8 @@ __device__ StepScalars step_prologue(const PcgState& st, int j, int k, const dou
     st.active[sc][j] = act;
     st.cbest[sc][j] = cb;
     st.itbest[sc][j] = ib;
+    st.csnap[sc][j] = out.snap ? csum : cs_prev;
+    st.cstop[j] = csum;
     st.relres[j] = rr;
     st.iters[j] = it;
     if (!act) st.status[j] = status;
@@ -111,6 +120,37 @@ __device__ double reduce_cols_strided(double v, double* red) {
   if (threadIdx.x < JJ)
     for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
   return s;
+}
+
+// out[jj] = sum_{p < np} part[p*k + j0 + jj] for jj < JJ, using the whole CTA
+// (fixed order: deterministic).  Valid in threads tid < JJ.
+template <int JJ>
+__device__ double sum_partials(const double* __restrict__ part, int np, int k, int j0, double* red) {
+  const int jj = threadIdx.x % JJ, P = blockDim.x / JJ, q = threadIdx.x / JJ;
+  double v = 0.0;
+#pragma unroll 4
+  for (int p = q; p < np; p += P) v += part[(int64_t)p * k + j0 + jj];
+  return reduce_cols_strided<JJ>(v, red);
+}
+
+// Same for a runtime number of columns k <= blockDim: out[j] = sum_p part[p*k + j],
+// written to out_s[j] (shared).  Tree over a power-of-two number of slices.
+__device__ void sum_partials_cols(const double* __restrict__ part, int np, int k, double* red, double* out_s) {
+  int P = 1;
+  while (P * 2 * k <= (int)blockDim.x) P *= 2;
+  const int j = threadIdx.x % k, q = threadIdx.x / k;
+  double v = 0.0;
+  if (q < P)
+    for (int p = q; p < np; p += P) v += part[(int64_t)p * k + j];
+  __syncthreads();
+  if (q < P) red[q * k + j] = v;
+  __syncthreads();
+  for (int h = P / 2; h >= 1; h >>= 1) {
+    if (q < h) red[q * k + j] += red[(q + h) * k + j];
+    __syncthreads();
+  }
+  if (threadIdx.x < k) out_s[threadIdx.x] = red[threadIdx.x];
+  __syncthreads();
 }
 
 // Every thread holds JJ partial sums (one per column); result in tid < JJ.
@@ -136,23 +176,25 @@ __device__ double reduce_cols_all(const double (&v)[JJ], double* red) {
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
 __global__ void __launch_bounds__(256)
-k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, T* g, T* u, T* w, T* S,
+k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ g,
+             T* __restrict__ u, T* __restrict__ w, T* __restrict__ S, T* __restrict__ wbest,
              PcgState st, const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Om_s = reinterpret_cast<T*>(smraw);
   T* U_s = Om_s + (int64_t)G * Gq;
   __shared__ double red[8 * 16];
   __shared__ double mu_s[JJ], lamp_s[JJ];
-  __shared__ int act_s[JJ], anyp_s;
+  __shared__ int act_s[JJ], snap_s[JJ], anyp_s;
   const int jg = blockIdx.z;
   if (threadIdx.x == 0) anyp_s = 0;
-  __syncthreads();
+  const double csum = sum_partials<JJ>(cpart, ncpart, k, jg * JJ, red);
   if (threadIdx.x < JJ) {
     const int j = jg * JJ + threadIdx.x;
-    const StepScalars sc = step_prologue(st, j, k, cpart, ncpart, blockIdx.x == 0);
+    const StepScalars sc = step_prologue(st, j, k, csum, blockIdx.x == 0);
     mu_s[threadIdx.x] = sc.mu;
     lamp_s[threadIdx.x] = sc.lam_prev;
     act_s[threadIdx.x] = sc.act;
+    snap_s[threadIdx.x] = sc.snap;
     if (sc.act_prev) atomicOr(&anyp_s, 1);
   }
   __syncthreads();
@@ -165,23 +207,53 @@ k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, 
   __syncthreads();
   for (int64_t t0 = r0; t0 < r1; t0 += TR) {
     const int tr = (int)((r1 - t0) < (int64_t)TR ? (r1 - t0) : (int64_t)TR);
-    // elementwise: w -= lam_prev u_old ; u = g + mu u_old (live columns)
-    const int ne = tr * G * JJ;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-      const int jj = e % JJ, rest = e / JJ;
-      const int i = rest % G, t = rest / G;
-      const int64_t gi = ((t0 + t) * G + i) * k + jg * JJ + jj;
-      // arithmetic in T: the float32 bulk path issues no float64 instruction
-      // per element (float64 throughput is 1/58 of float32 on this part)
-      const T uo = u[gi];
-      const T lp = (T)lamp_s[jj];
-      if (lp != (T)0) w[gi] = w[gi] - lp * uo;
-      T un = uo;
-      if (act_s[jj]) {
-        un = g[gi] + (T)mu_s[jj] * uo;
-        u[gi] = un;
+    // elementwise: w -= lam_prev u_old ; u = g + mu u_old (live columns).
+    // Arithmetic in T: the float32 bulk path issues no float64 instruction
+    // per element (float64 throughput is 1/58 of float32 on this part).
+    // Units of V consecutive right-hand sides, EB units per thread in flight.
+    constexpr int V = (JJ >= 4) ? 4 : JJ;
+    constexpr int EB = 4;
+    const int nu = tr * G * (JJ / V);
+    for (int e0 = threadIdx.x; e0 < nu; e0 += EB * blockDim.x) {
+      T uo[EB][V], gv[EB][V], wv[EB][V];
+      int64_t gi[EB];
+      int ee[EB];
+#pragma unroll
+      for (int b = 0; b < EB; ++b) {
+        const int e = e0 + b * blockDim.x;
+        ee[b] = e;
+        if (e < nu) {
+          const int jv = e % (JJ / V), rest = e / (JJ / V);
+          const int i = rest % G, t = rest / G;
+          gi[b] = ((t0 + t) * G + i) * k + jg * JJ + jv * V;
+#pragma unroll
+          for (int c = 0; c < V; ++c) {
+            uo[b][c] = u[gi[b] + c];
+            gv[b][c] = g[gi[b] + c];
+            wv[b][c] = w[gi[b] + c];
+          }
+        }
       }
-      U_s[e] = un;
+#pragma unroll
+      for (int b = 0; b < EB; ++b) {
+        if (ee[b] < nu) {
+          const int jv = ee[b] % (JJ / V);
+#pragma unroll
+          for (int c = 0; c < V; ++c) {
+            const int jj = jv * V + c;
+            const T lp = (T)lamp_s[jj];
+            T un = uo[b][c];
+            const T wn = wv[b][c] - lp * un;
+            if (lp != (T)0) w[gi[b] + c] = wn;
+            if (snap_s[jj]) wbest[gi[b] + c] = wn;
+            if (act_s[jj]) {
+              un = gv[b][c] + (T)mu_s[jj] * un;
+              u[gi[b] + c] = un;
+            }
+            U_s[(int64_t)ee[b] * V + c] = un;
+          }
+        }
+      }
     }
     __syncthreads();
     // S = U Omega on the tile; thread item (t, hq, jj) with jj = tid % JJ
@@ -341,11 +413,11 @@ k_reduce(int64_t nidx, int nrb, const T* __restrict__ Cpart, T* __restrict__ C, 
     // scalar step for all k columns
     const int it = *st.it;
     const int slot = it & 1;
+    __shared__ double red_s[256], dsum_s[kMaxRhs];
     if (threadIdx.x == 0) nact_s = 0;
-    __syncthreads();
+    sum_partials_cols(dpart, ndpart, k, red_s, dsum_s);
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-      double d = 0.0;
-      for (int p = 0; p < ndpart; ++p) d += dpart[(int64_t)p * k + j];
+      const double d = dsum_s[j];
       int act = st.active[slot][j];
       double lam = 0.0;
       if (act) {
@@ -388,69 +460,111 @@ k_reduce(int64_t nidx, int nrb, const T* __restrict__ Cpart, T* __restrict__ C, 
 // ---------------------------------------------------------------------------
 // proj_update: t = S - Q C;  g = alpha g - lam_j t;  partials of g^T g.
 // lam_j = lam[j] when lam != nullptr, else lam_const.
-// grid (nrb, 1, k / JJ); thread item = (row, block), block index fastest.
+// grid (n_update row ranges, n_ugroups block groups, k / JJ).  A block group
+// is a run of whole blocks; thread q of the CTA owns one column quad of the
+// group and keeps its 4 x JJ entries of C in registers.  Per row tile:
+//   phase 1  part[r][q][jj] = sum_{c < 4} Q[t, 4q + c] C[4q + c, jj]
+//   phase 2  t[r, i, jj] = S[t, i, jj] - sum_{q in block i} part[r][q][jj]
+// so Q streams once with coalesced 16-byte loads and every C value is read
+// from L2 once per CTA.
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
-__global__ void __launch_bounds__(256)
-k_proj_update(int64_t M, int G, int np, int k, const T* __restrict__ Q, const T* __restrict__ S, T* g,
-              const T* __restrict__ C, const int* __restrict__ n_i, const int* __restrict__ poff, int alpha,
-              const double* __restrict__ lam, double lam_const, double* __restrict__ cpart, PcgState st,
-              int use_state) {
-  __shared__ double red[8 * 16];
-  const int jg = blockIdx.z;
+__global__ void __launch_bounds__(512)
+k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q, const T* __restrict__ S,
+              T* __restrict__ g, const T* __restrict__ C, const int* __restrict__ poff,
+              const int* __restrict__ ug_blk0, int alpha, const double* __restrict__ lam, double lam_const,
+              double* __restrict__ cpart, PcgState st, int use_state) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* part = reinterpret_cast<T*>(smraw);
+  __shared__ double red[16 * 16];
+  __shared__ T lam_s[JJ];
+  const int jg = blockIdx.z, grp = blockIdx.y;
+  const int64_t cp_idx = ((int64_t)blockIdx.x * gridDim.y + grp) * k + jg * JJ;
   if (use_state) {
     const int slot = (*st.it - 1) & 1;   // reduce has already advanced the counter
     int any = 0;
     for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jg * JJ + jj];
     if (!any) {
-      if (threadIdx.x < JJ) cpart[(int64_t)blockIdx.x * k + jg * JJ + threadIdx.x] = 0.0;
+      if (threadIdx.x < JJ) cpart[cp_idx + threadIdx.x] = 0.0;
       return;
     }
   }
-  T lam_r[JJ];
+  if (threadIdx.x < JJ) lam_s[threadIdx.x] = (T)(lam ? lam[jg * JJ + threadIdx.x] : lam_const);
+  const int b0 = ug_blk0[grp], b1 = ug_blk0[grp + 1];
+  const int q0 = poff[b0] >> 2, nqg = (poff[b1] >> 2) - q0, nbg = b1 - b0;
+  const int tid = threadIdx.x;
+  T creg[4][JJ];
+  if (tid < nqg) {
 #pragma unroll
-  for (int jj = 0; jj < JJ; ++jj) lam_r[jj] = (T)(lam ? lam[jg * JJ + jj] : lam_const);
+    for (int c = 0; c < 4; ++c) {
+      const T* cr = C + (int64_t)(4 * (q0 + tid) + c) * k + jg * JJ;
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) creg[c][jj] = cr[jj];
+    }
+  }
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
-  const int64_t nitems = (r1 - r0) * G;
-  T cs[JJ];
+  const int jj_t = tid % JJ;
+  T cs = 0;
+  __syncthreads();
+  for (int64_t t0 = r0; t0 < r1; t0 += TRB) {
+    const int tr = (int)((r1 - t0) < (int64_t)TRB ? (r1 - t0) : (int64_t)TRB);
+    if (tid < nqg) {
+      const T* qp = Q + t0 * np + 4 * (q0 + tid);
+      for (int r = 0; r < tr; r += 2) {
+        T qv[2][4];
+        Vec4<T>::load(qp + (int64_t)r * np, qv[0]);
+        if (r + 1 < tr) Vec4<T>::load(qp + (int64_t)(r + 1) * np, qv[1]);
 #pragma unroll
-  for (int jj = 0; jj < JJ; ++jj) cs[jj] = 0;
-  for (int64_t it = threadIdx.x; it < nitems; it += blockDim.x) {
-    const int i = (int)(it % G);
-    const int64_t t = r0 + it / G;
-    const int64_t base = (t * G + i) * k + jg * JJ;
-    T acc[JJ];
+        for (int h = 0; h < 2; ++h) {
+          if (r + h < tr) {
+            T* dst = part + ((int64_t)(r + h) * nqg + tid) * JJ;
 #pragma unroll
-    for (int jj = 0; jj < JJ; ++jj) acc[jj] = S[base + jj];
-    const int nqi = (n_i[i] + 3) >> 2;
-    const int pc = poff[i];
-    const T* qrow = Q + t * np + pc;
-    for (int qq = 0; qq < nqi; ++qq) {
-      T qv[4];
-      Vec4<T>::load(qrow + 4 * qq, qv);
+            for (int jj = 0; jj < JJ; ++jj) {
+              T acc = qv[h][0] * creg[0][jj];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const T* cr = C + (int64_t)(pc + 4 * qq + c) * k + jg * JJ;
-#pragma unroll
-        for (int jj = 0; jj < JJ; ++jj) acc[jj] -= qv[c] * __ldg(cr + jj);
+              for (int c = 1; c < 4; ++c) acc += qv[h][c] * creg[c][jj];
+              dst[jj] = acc;
+            }
+          }
+        }
       }
     }
-    T gl[JJ];
+    __syncthreads();
+    const int nout = tr * nbg * JJ;
+    constexpr int EB = 4;
+    for (int o0 = tid; o0 < nout; o0 += EB * blockDim.x) {
+      T sv[EB], gv[EB];
+      int64_t gi[EB];
 #pragma unroll
-    for (int jj = 0; jj < JJ; ++jj) {
-      const T gold = alpha ? g[base + jj] : (T)0;
-      const T gn = gold - lam_r[jj] * acc[jj];
-      gl[jj] = gn;
-      cs[jj] += gn * gn;
+      for (int b = 0; b < EB; ++b) {
+        const int o = o0 + b * blockDim.x;
+        gi[b] = -1;
+        if (o < nout) {
+          const int rest = o / JJ, ib = rest % nbg, r = rest / nbg;
+          gi[b] = ((t0 + r) * G + b0 + ib) * k + jg * JJ + (o % JJ);
+          sv[b] = S[gi[b]];
+          gv[b] = alpha ? g[gi[b]] : (T)0;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < EB; ++b) {
+        const int o = o0 + b * blockDim.x;
+        if (o < nout) {
+          const int jj = o % JJ, rest = o / JJ, ib = rest % nbg, r = rest / nbg;
+          const int qa = (poff[b0 + ib] >> 2) - q0, qb = (poff[b0 + ib + 1] >> 2) - q0;
+          T sum = 0;
+          const T* pr = part + (int64_t)r * nqg * JJ + jj;
+          for (int qq = qa; qq < qb; ++qq) sum += pr[qq * JJ];
+          const T gn = gv[b] - lam_s[jj] * (sv[b] - sum);
+          g[gi[b]] = gn;
+          cs += gn * gn;
+        }
+      }
     }
-#pragma unroll
-    for (int jj = 0; jj < JJ; ++jj) g[base + jj] = gl[jj];
+    __syncthreads();
   }
-  double csd[JJ];
-#pragma unroll
-  for (int jj = 0; jj < JJ; ++jj) csd[jj] = (double)cs[jj];
-  const double s = reduce_cols_all<JJ>(csd, red);
-  if (threadIdx.x < JJ) cpart[(int64_t)blockIdx.x * k + jg * JJ + threadIdx.x] = s;
+  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  if (tid < JJ) cpart[cp_idx + tid] = tot;
 }
 
 // ---------------------------------------------------------------------------
@@ -603,6 +717,26 @@ __global__ void k_add_int(int n, const int* __restrict__ a, int* __restrict__ ac
   if (j < n) acc[j] += a[j];
 }
 
+// After a run: columns that stopped without converging and whose saved w has
+// a smaller c than the final one take the saved w (best iterate).
+template <typename T>
+__global__ void k_restore_best(int64_t n, int k, PcgState st, const T* __restrict__ wbest, T* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % k);
+    const int slot = (*st.it) & 1;
+    const double cs = st.csnap[slot][j] < st.csnap[slot ^ 1][j] ? st.csnap[slot][j] : st.csnap[slot ^ 1][j];
+    if (st.status[j] != GLM_SUR_OK && st.status[j] != kStatusRunning && !(st.cstop[j] <= cs)) w[e] = wbest[e];
+  }
+}
+__global__ void k_restore_relres(int k, PcgState st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  const int slot = (*st.it) & 1;
+  const double cs = st.csnap[slot][j] < st.csnap[slot ^ 1][j] ? st.csnap[slot][j] : st.csnap[slot ^ 1][j];
+  if (st.status[j] != GLM_SUR_OK && st.status[j] != kStatusRunning && !(st.cstop[j] <= cs) && st.c1[j] > 0)
+    st.relres[j] = sqrt(cs / st.c1[j]);
+}
+
 // finalize sums of partials: out[j] = sqrt(sum_p part[p*k+j])
 __global__ void k_sum_partials_sqrt(int np_, int k, const double* __restrict__ part, double* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -629,11 +763,11 @@ __global__ void k_unpad_q(int64_t M, int G, int np, const int* __restrict__ off,
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
 static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
-                                 const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
+                                 T* wbest, const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
   dim3 grid(p.n_sigma, 1, k / JJ);
   const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
-  k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, st, cpart, p.n_update,
-                                              dpart);
+  k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, wbest, st, cpart,
+                                              p.n_cpart, dpart);
 }
 
 template <typename T, int JJ>
@@ -658,9 +792,10 @@ template <typename T, int JJ>
 static void launch_proj_update_jj(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g,
                                   const T* C, int alpha, const double* lam, double lam_const, double* cpart,
                                   const PcgState& st, int use_state, cudaStream_t s) {
-  dim3 grid(p.n_update, 1, k / JJ);
-  k_proj_update<T, JJ><<<grid, 256, 0, s>>>(gm.M, gm.G, gm.np, k, Q, S, g, C, gm.d_n_i, gm.d_poff, alpha, lam,
-                                            lam_const, cpart, st, use_state);
+  dim3 grid(p.n_update, p.n_ugroups, k / JJ);
+  const size_t smem = sizeof(T) * (size_t)p.TRB * p.ug_max_quads * JJ;
+  k_proj_update<T, JJ><<<grid, p.ug_threads, smem, s>>>(gm.M, gm.G, gm.np, k, p.TRB, Q, S, g, C, gm.d_poff,
+                                                         gm.d_ug_blk0, alpha, lam, lam_const, cpart, st, use_state);
 }
 
 #define GS_DISPATCH_JJ(JJv, CALL) \
@@ -673,9 +808,9 @@ static void launch_proj_update_jj(const IterPlan& p, const Geom& gm, int k, cons
   }
 
 template <typename T>
-void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
+void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S, T* wbest,
                        const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
-#define C_(J) launch_sigma_step_jj<T, J>(p, gm, k, Om, g, u, w, S, st, cpart, dpart, s)
+#define C_(J) launch_sigma_step_jj<T, J>(p, gm, k, Om, g, u, w, S, wbest, st, cpart, dpart, s)
   GS_DISPATCH_JJ(p.JJ, C_)
 #undef C_
 }
@@ -739,11 +874,11 @@ template void launch_add_to_f64<float>(int64_t, const float*, double*, cudaStrea
 template void launch_add_to_f64<double>(int64_t, const double*, double*, cudaStream_t);
 void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, float* g,
                        float* u, float* w, double* cpart, cudaStream_t s) {
-  k_init_inner<<<p.n_update, 256, 0, s>>>(gm.M, gm.G * k, k, rho, live, g, u, w, cpart);
+  k_init_inner<<<p.n_cpart, 256, 0, s>>>(gm.M, gm.G * k, k, rho, live, g, u, w, cpart);
 }
 template <typename T>
 void launch_colsumsq(const IterPlan& p, const Geom& gm, int k, const T* v, double* part, cudaStream_t s) {
-  k_colsumsq<T><<<p.n_update, 256, 0, s>>>(gm.M, gm.G * k, k, v, part);
+  k_colsumsq<T><<<p.n_cpart, 256, 0, s>>>(gm.M, gm.G * k, k, v, part);
 }
 void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, cudaStream_t s) {
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(gm.M * 8, 256), 4096), gm.G);
@@ -756,6 +891,13 @@ void launch_masked_axpy(int64_t n, int k, const int* mask, double sign, const do
 void launch_shift_diag(int G, int Gq, const double* Om64, float* Om32, double rel, cudaStream_t s) {
   k_shift_diag<<<1, 32, 0, s>>>(G, Gq, Om64, Om32, rel);
 }
+template <typename T>
+void launch_restore_best(int64_t n, int k, const PcgState& st, const T* wbest, T* w, cudaStream_t s) {
+  k_restore_best<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, s>>>(n, k, st, wbest, w);
+  k_restore_relres<<<1, 64, 0, s>>>(k, st);
+}
+template void launch_restore_best<float>(int64_t, int, const PcgState&, const float*, float*, cudaStream_t);
+template void launch_restore_best<double>(int64_t, int, const PcgState&, const double*, double*, cudaStream_t);
 void launch_add_int(int n, const int* a, int* acc, cudaStream_t s) {
   k_add_int<<<(unsigned)ceil_div(n, 64), 64, 0, s>>>(n, a, acc);
 }
@@ -764,12 +906,14 @@ void launch_sum_partials_sqrt(int np_, int k, const double* part, double* out, c
 }
 
 template <typename T>
-cudaError_t set_smem_attrs(int JJ, size_t bytes) {
+cudaError_t set_smem_attrs(int JJ, size_t bytes, size_t upd_bytes) {
   cudaError_t e = cudaSuccess;
 #define C_(J)                                                                                                    \
   e = cudaFuncSetAttribute(k_sigma_step<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);        \
   if (e == cudaSuccess)                                                                                          \
-    e = cudaFuncSetAttribute(k_sigma_resid<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(k_sigma_resid<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);     \
+  if (e == cudaSuccess)                                                                                          \
+    e = cudaFuncSetAttribute(k_proj_update<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_bytes);
   GS_DISPATCH_JJ(JJ, C_)
 #undef C_
   return e;
@@ -777,9 +921,9 @@ cudaError_t set_smem_attrs(int JJ, size_t bytes) {
 
 // explicit instantiations
 template void launch_sigma_step<double>(const IterPlan&, const Geom&, int, const double*, double*, double*, double*,
-                                        double*, const PcgState&, const double*, double*, cudaStream_t);
+                                        double*, double*, const PcgState&, const double*, double*, cudaStream_t);
 template void launch_sigma_step<float>(const IterPlan&, const Geom&, int, const float*, float*, float*, float*,
-                                       float*, const PcgState&, const double*, double*, cudaStream_t);
+                                       float*, float*, const PcgState&, const double*, double*, cudaStream_t);
 template void launch_sigma_resid<double>(const IterPlan&, const Geom&, int, const double*, const double*,
                                          const double*, double*, cudaStream_t);
 template void launch_proj_partial<double>(const IterPlan&, const Geom&, int, const double*, const double*, double*,
@@ -802,7 +946,7 @@ template void launch_layout_to_colmajor<double>(const Geom&, int, const double*,
 template void launch_convert<double, float>(int64_t, const double*, float*, double, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);
 template void launch_colsumsq<double>(const IterPlan&, const Geom&, int, const double*, double*, cudaStream_t);
-template cudaError_t set_smem_attrs<double>(int, size_t);
-template cudaError_t set_smem_attrs<float>(int, size_t);
+template cudaError_t set_smem_attrs<double>(int, size_t, size_t);
+template cudaError_t set_smem_attrs<float>(int, size_t, size_t);
 
 }  // namespace glmsur

@@ -16,13 +16,21 @@ struct IterPlan {
   int n_sigma = 1;         // row CTAs of the Sigma-apply kernels (d partials)
   int n_partial_rows = 1;  // row ranges of proj_partial (C partials)
   int n_qgroups = 1;       // column-quad groups of proj_partial
-  int n_update = 1;        // row CTAs of proj_update (c partials)
+  int n_update = 1;        // row CTAs of proj_update
+  int n_ugroups = 1;       // block groups of proj_update
+  int n_cpart = 1;         // c partials written per step (n_update * n_ugroups)
+  int ug_threads = 32;     // threads of a proj_update CTA (>= quads of any group)
+  int ug_max_quads = 1;    // quads of the largest block group
+  int TRB = 1;             // rows per proj_update tile
   size_t sigma_smem = 0;
+  size_t update_smem = 0;
 };
 
 template <typename T>
-void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
+void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S, T* wbest,
                        const PcgState& st, const double* cpart, double* dpart, cudaStream_t s);
+template <typename T>
+void launch_restore_best(int64_t n, int k, const PcgState& st, const T* wbest, T* w, cudaStream_t s);
 template <typename T>
 void launch_sigma_resid(const IterPlan& p, const Geom& gm, int k, const T* Om, const T* Y, const T* W, T* E,
                         cudaStream_t s);
@@ -58,6 +66,6 @@ void launch_add_int(int n, const int* a, int* acc, cudaStream_t s);
 void launch_shift_diag(int G, int Gq, const double* Om64, float* Om32, double rel, cudaStream_t s);
 void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, cudaStream_t s);
 template <typename T>
-cudaError_t set_smem_attrs(int JJ, size_t bytes);
+cudaError_t set_smem_attrs(int JJ, size_t bytes, size_t upd_bytes);
 
 }  // namespace glmsur

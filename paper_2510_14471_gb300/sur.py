@@ -29,8 +29,8 @@ class GlmSur:
     """SUR model handle: X_i factored once (TSQR on the device), Omega kept
     on the device; ``solve`` runs PCG-Aug for k right-hand sides."""
 
-    def __init__(self, X_blocks, Omega, precision: str = "fp64", tol: float = 1e-12, maxit: int = 0,
-                 stagnation_window: int = 10, inner_tol: float = 1e-5, max_refine: int = 8,
+    def __init__(self, X_blocks, Omega, precision: str = "fp64", tol: float = 1e-13, maxit: int = 0,
+                 stagnation_window: int = 25, inner_tol: float = 1e-5, max_refine: int = 8,
                  chunk: int = 16, inner_shift: float = 1e-6, device="cuda"):
         self.device = torch.device(device)
         blocks = [_dev_f64(x, self.device) for x in X_blocks]
