@@ -75,7 +75,7 @@ typedef struct {
 } glm_sur_opts;
 
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
- * max_refine 8, chunk 16, inner_shift 1e-6.  A column that stops without
+ * max_refine 8, chunk 16, inner_shift 0.  A column that stops without
  * converging (stagnation, breakdown, maxit) returns its best saved iterate:
  * w is saved whenever c falls below a quarter of the c of the previous save. */
 void glm_sur_default_opts(glm_sur_opts* opts);

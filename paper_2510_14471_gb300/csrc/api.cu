@@ -137,11 +137,73 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   p.ug_threads = (int)std::min<int64_t>(512, ceil_div(gm.ug_max_quads, 32) * 32);
   p.n_update = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, (int64_t)njg * p.n_ugroups)));
   p.n_cpart = p.n_update * p.n_ugroups;
-  const size_t upd_row = sz * (size_t)gm.ug_max_quads * p.JJ;
+  const size_t upd_row = sz * (size_t)(gm.ug_max_quads + 32) * p.JJ;   // padded quad stride
   p.TRB = (int)std::max<size_t>(2, std::min<size_t>(32, (48 * 1024) / upd_row));
   p.update_smem = (size_t)p.TRB * upd_row;
+  // TMA-streamed step kernels: one CTA per SM, whole rows (all k) per tile
+  const size_t GK_bytes = sz * (size_t)gm.G * k;
+  const size_t budget_tma = 200 * 1024;
+  if (p.JJ == k && GK_bytes % 16 == 0) {
+    // Sigma step: items are (RI-row group, column quad of Omega, rhs); pick RI
+    // and the tile height TR so that a tile holds >= 512 items when shared
+    // memory allows (3 stages, else 2)
+    const size_t om = sz * (size_t)gm.G * gm.Gq;
+    const size_t sig_budget = 210 * 1024;
+    const int per_row_items = (gm.Gq / 4) * p.JJ;
+    p.ri = per_row_items >= 256 ? 4 : (per_row_items >= 64 ? 2 : 1);
+    int tr_want = p.ri * (int)ceil_div(512, per_row_items);
+    tr_want = std::max(p.ri, std::min(64, tr_want));
+    for (int tr = tr_want; tr >= 1 && !p.tma_sigma; tr = (tr > p.ri ? tr - p.ri : tr - 1)) {
+      for (int nst = 3; nst >= 2; --nst) {
+        if (128 + om + (size_t)nst * tr * 3 * GK_bytes <= sig_budget) {
+          p.tr_tma = tr; p.nst_sigma = nst; p.tma_sigma = true;
+          break;
+        }
+      }
+    }
+    if (p.tma_sigma) p.sigma_tma_smem = 128 + om + (size_t)p.nst_sigma * p.tr_tma * 3 * GK_bytes;
+    if (gm.n_ugroups == 1) {
+      p.nst_update = 3;
+      const size_t row_stage = sz * (size_t)gm.np + 2 * GK_bytes, row_part = sz * (size_t)(gm.nq + 32) * p.JJ;
+      const size_t per_row = p.nst_update * row_stage + row_part;
+      if (per_row + 128 <= budget_tma) {
+        p.trb_tma = (int)std::min<size_t>(16, (budget_tma - 128) / per_row);
+        p.tma_update = true;
+        p.update_tma_smem = 128 + (size_t)p.trb_tma * per_row;
+        p.update_threads = (int)std::max<int64_t>(256, std::min<int64_t>(512, ceil_div(gm.nq, 32) * 32));
+      }
+    }
+    // block x column update: every block at most 32 columns, G*k pairs on <= 2 per thread
+    int nmax = 0;
+    for (int v : h->n_i) nmax = std::max(nmax, v);
+    const int npairs = gm.G * k;
+    if (nmax <= 32 && npairs <= 1024 && (!is_double || npairs <= 512)) {
+      p.bj_np = npairs > 512 ? 2 : 1;
+      p.nst_bj = 3;
+      const size_t row_stage = sz * (size_t)gm.np + 2 * GK_bytes;
+      const size_t trb = (budget_tma - 128) / (p.nst_bj * row_stage);
+      if (trb >= 1) {
+        p.trb_bj = (int)std::min<size_t>(16, trb);
+        p.bj_smem = 128 + (size_t)p.nst_bj * p.trb_bj * row_stage;
+        p.bj_update = true;
+        p.tma_update = true;   // same grid and partial layout
+      }
+    }
+    if (p.tma_sigma) p.n_sigma = h->sms;
+    if (p.tma_update) {
+      p.n_update = h->sms;
+      p.n_cpart = h->sms;
+    }
+  }
   cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem, p.update_smem)
                             : set_smem_attrs<float>(p.JJ, p.sigma_smem, p.update_smem);
+  if (e == cudaSuccess && (p.tma_sigma || p.tma_update))
+    e = is_double ? set_tma_smem_attrs<double>(p.JJ, std::max<size_t>(p.sigma_tma_smem, 1024),
+                                               std::max<size_t>(p.update_tma_smem, 1024),
+                                               std::max<size_t>(p.bj_smem, 1024))
+                  : set_tma_smem_attrs<float>(p.JJ, std::max<size_t>(p.sigma_tma_smem, 1024),
+                                              std::max<size_t>(p.update_tma_smem, 1024),
+                                              std::max<size_t>(p.bj_smem, 1024));
   if (e != cudaSuccess) {
     set_last_error(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
     return GLM_SUR_CUDA_ERROR;
@@ -195,7 +257,7 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   if (h->opts.precision != GLM_SUR_PREC_FP64) GS_CUDA_TRY(dalloc(&h->d64, mk));
   // doubles: c[2], c1, lam, relres, cbest[2];  ints: active[2], iters, status, itbest[2], it, done
   GS_CUDA_TRY(dalloc(&h->st_buf, (size_t)kStateDoubles * k));
-  GS_CUDA_TRY(dalloc(&h->st_ibuf, (size_t)kStateInts * k + 2));
+  GS_CUDA_TRY(dalloc(&h->st_ibuf, (size_t)kStateInts * k + 3));
   GS_CUDA_TRY(dalloc(&h->d_status_final, (size_t)k));
   GS_CUDA_TRY(dalloc(&h->d_iters_acc, (size_t)k));
   GS_CUDA_TRY(dalloc(&h->d_mask, (size_t)2 * k));
@@ -220,6 +282,7 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   st.itbest[1] = h->st_ibuf + 5 * k;
   st.it = h->st_ibuf + 6 * k;
   st.done = h->st_ibuf + 6 * k + 1;
+  st.err = h->st_ibuf + 6 * k + 2;
   h->kcap = k;
   return GLM_SUR_OK;
 }
@@ -233,6 +296,7 @@ glm_sur_status reset_state(glm_sur_ctx* h, int k, double tol, int maxit, int W, 
   st.W = W;
   GS_CUDA_TRY(cudaMemsetAsync(h->st_buf, 0, sizeof(double) * (size_t)kStateDoubles * h->kcap, s));
   GS_CUDA_TRY(cudaMemsetAsync(h->st_ibuf, 0, sizeof(int) * ((size_t)kStateInts * h->kcap + 2), s));
+  // (the error word after them is cleared per solve, not per inner run)
   return GLM_SUR_OK;
 }
 
@@ -301,11 +365,12 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
   for (int64_t c = 0; c < max_launch; ++c) {
     GS_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
     h->launches += 4 * (int64_t)chunk;
-    GS_CUDA_TRY(cudaMemcpyAsync(&h->h_done[c & 1], h->st.done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // done flag and error word side by side: h_done[2*slot], h_done[2*slot + 1]
+    GS_CUDA_TRY(cudaMemcpyAsync(&h->h_done[2 * (c & 1)], h->st.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA_TRY(cudaEventRecord(h->ev[c & 1], s));
     if (c >= 1) {
       GS_CUDA_TRY(cudaEventSynchronize(h->ev[(c - 1) & 1]));
-      if (h->h_done[(c - 1) & 1]) break;
+      if (h->h_done[2 * ((c - 1) & 1)] || h->h_done[2 * ((c - 1) & 1) + 1]) break;
     }
   }
   // columns that stopped without converging keep their best saved w
@@ -386,7 +451,7 @@ void glm_sur_default_opts(glm_sur_opts* o) {
   o->inner_tol = 1e-5;
   o->max_refine = 8;
   o->chunk = 16;
-  o->inner_shift = 1e-6;
+  o->inner_shift = 0.0;
 }
 
 const char* glm_sur_status_string(glm_sur_status s) {
@@ -479,7 +544,7 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   SETUP_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   SETUP_TRY(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
   SETUP_TRY(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
-  SETUP_TRY(cudaMallocHost(&h->h_done, 2 * sizeof(int)));
+  SETUP_TRY(cudaMallocHost(&h->h_done, 4 * sizeof(int)));
   SETUP_TRY(cudaMallocHost(&h->h_norms, 2 * kMaxRhs * sizeof(double)));
   SETUP_TRY(dalloc(&gm.d_n_i, G));
   SETUP_TRY(dalloc(&gm.d_off, G + 1));
@@ -587,6 +652,7 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
   }
   const int64_t mk = m * k;
   const int maxit = h->opts.maxit > 0 ? h->opts.maxit : (int)std::min<int64_t>(m - gm.n + 1, 1 << 30);
+  GS_CUDA_TRY(cudaMemsetAsync(h->st.err, 0, sizeof(int), s));
   launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
   h->launches += 1;
   GS_CUDA_TRY(cudaGetLastError());
@@ -687,6 +753,12 @@ glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
   if (!h || !status || k < 1 || k > h->last_k) return GLM_SUR_INVALID_ARG;
   GS_CUDA_TRY(cudaDeviceSynchronize());
   GS_CUDA_TRY(cudaMemcpy(status, h->d_status_final, k * sizeof(int), cudaMemcpyDeviceToHost));
+  int err = 0;
+  GS_CUDA_TRY(cudaMemcpy(&err, h->st.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    for (int j = 0; j < k; ++j) status[j] = GLM_SUR_TIMEOUT;
+    return GLM_SUR_TIMEOUT;
+  }
   glm_sur_status worst = GLM_SUR_OK;
   for (int j = 0; j < k; ++j) {
     if (status[j] == kStatusRunning) status[j] = GLM_SUR_NOT_CONVERGED;

@@ -83,6 +83,7 @@ struct PcgState {
   double* relres = nullptr;
   int* it = nullptr;                   // completed steps (written by the reduce kernel)
   int* done = nullptr;
+  int* err = nullptr;                  // set when a bounded device wait gave up
 };
 
 }  // namespace glmsur

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "pcg.h"
+#include "tma.cuh"
 
 namespace glmsur {
 
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256)
 k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ g,
              T* __restrict__ u, T* __restrict__ w, T* __restrict__ S, T* __restrict__ wbest,
              PcgState st, const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T* Om_s = reinterpret_cast<T*>(smraw);
   T* U_s = Om_s + (int64_t)G * Gq;
   __shared__ double red[8 * 16];
@@ -294,7 +295,7 @@ template <typename T, int JJ>
 __global__ void __launch_bounds__(256)
 k_sigma_resid(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ Y,
               const T* __restrict__ Wv, T* E) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T* Om_s = reinterpret_cast<T*>(smraw);
   T* U_s = Om_s + (int64_t)G * Gq;
   const int jg = blockIdx.z;
@@ -474,7 +475,7 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
               T* __restrict__ g, const T* __restrict__ C, const int* __restrict__ poff,
               const int* __restrict__ ug_blk0, int alpha, const double* __restrict__ lam, double lam_const,
               double* __restrict__ cpart, PcgState st, int use_state) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T* part = reinterpret_cast<T*>(smraw);
   __shared__ double red[16 * 16];
   __shared__ T lam_s[JJ];
@@ -492,6 +493,7 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
   if (threadIdx.x < JJ) lam_s[threadIdx.x] = (T)(lam ? lam[jg * JJ + threadIdx.x] : lam_const);
   const int b0 = ug_blk0[grp], b1 = ug_blk0[grp + 1];
   const int q0 = poff[b0] >> 2, nqg = (poff[b1] >> 2) - q0, nbg = b1 - b0;
+  const int nqp = nqg + ((33 - (nqg & 31)) & 31);   // padded so that nqp % 32 == 1
   const int tid = threadIdx.x;
   T creg[4][JJ];
   if (tid < nqg) {
@@ -503,8 +505,7 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
     }
   }
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
-  const int jj_t = tid % JJ;
-  T cs = 0;
+    T cs = 0;
   __syncthreads();
   for (int64_t t0 = r0; t0 < r1; t0 += TRB) {
     const int tr = (int)((r1 - t0) < (int64_t)TRB ? (r1 - t0) : (int64_t)TRB);
@@ -517,13 +518,13 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (r + h < tr) {
-            T* dst = part + ((int64_t)(r + h) * nqg + tid) * JJ;
+            T* dst = part + (int64_t)(r + h) * JJ * nqp + tid;
 #pragma unroll
             for (int jj = 0; jj < JJ; ++jj) {
               T acc = qv[h][0] * creg[0][jj];
 #pragma unroll
               for (int c = 1; c < 4; ++c) acc += qv[h][c] * creg[c][jj];
-              dst[jj] = acc;
+              dst[(int64_t)jj * nqp] = acc;
             }
           }
         }
@@ -553,8 +554,8 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
           const int jj = o % JJ, rest = o / JJ, ib = rest % nbg, r = rest / nbg;
           const int qa = (poff[b0 + ib] >> 2) - q0, qb = (poff[b0 + ib + 1] >> 2) - q0;
           T sum = 0;
-          const T* pr = part + (int64_t)r * nqg * JJ + jj;
-          for (int qq = qa; qq < qb; ++qq) sum += pr[qq * JJ];
+          const T* pr = part + (int64_t)(r * JJ + jj) * nqp;
+          for (int qq = qa; qq < qb; ++qq) sum += pr[qq];
           const T gn = gv[b] - lam_s[jj] * (sv[b] - sum);
           g[gi[b]] = gn;
           cs += gn * gn;
@@ -565,6 +566,402 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
   }
   const double tot = reduce_cols_strided<JJ>((double)cs, red);
   if (tid < JJ) cpart[cp_idx + tid] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// TMA-streamed variants (all k right-hand sides in one CTA: JJ == k, row
+// length G*k*sizeof(T) a multiple of 16 bytes).  One CTA per SM processes a
+// contiguous row range in tiles; each tile's rows (contiguous in HBM) are
+// brought into shared memory by 1-D bulk copies (cp.async.bulk) completing on
+// an mbarrier, NST tiles in flight, so the CTA streams at HBM rate with few
+// warps.  Waits are bounded: on timeout the CTA records an error and stops.
+// ---------------------------------------------------------------------------
+
+// Thread 0: wait for the tiles still in flight (bounded) before leaving.
+__device__ void tma_drain(uint64_t* full, int NST, int next_tile, int issued) {
+  for (int t = next_tile; t < issued; ++t) mbar_wait_bounded(&full[t % NST], (t / NST) & 1, kWaitLimitNs);
+}
+
+template <typename T, int JJ>
+__global__ void __launch_bounds__(512, 1)
+k_proj_update_tma(int64_t M, int G, int np, int nq, int TRB, int NST, const T* __restrict__ Q,
+                  const T* __restrict__ S, T* __restrict__ g, const T* __restrict__ C, const int* __restrict__ poff,
+                  int alpha, const double* __restrict__ lam, double lam_const, double* __restrict__ cpart,
+                  PcgState st, int use_state) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+  T* stage0 = reinterpret_cast<T*>(smraw + 128);
+  const int64_t GK = (int64_t)G * JJ;
+  const int64_t stage_elems = (int64_t)TRB * (np + (alpha ? 2 : 1) * GK);
+  T* part = stage0 + NST * stage_elems;
+  const int nqp = nq + ((33 - (nq & 31)) & 31);   // padded so that nqp % 32 == 1
+  __shared__ double red[16 * 16];
+  __shared__ T lam_s[JJ];
+  __shared__ int abort_s;
+  const int tid = threadIdx.x;
+  if (*st.err) return;   // an earlier bounded wait gave up: the run is being abandoned
+  if (use_state) {
+    const int slot = (*st.it - 1) & 1;   // reduce has already advanced the counter
+    int any = 0;
+    for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jj];
+    if (!any) {
+      if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = 0.0;
+      return;
+    }
+  }
+  if (tid < JJ) lam_s[tid] = (T)(lam ? lam[tid] : lam_const);
+  T creg[4][JJ];
+  if (tid < nq) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const T* cr = C + (int64_t)(4 * tid + c) * JJ;
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) creg[c][jj] = cr[jj];
+    }
+  }
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int ntiles = (int)((r1 - r0 + TRB - 1) / TRB);
+  if (tid == 0) {
+    for (int q = 0; q < NST; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int tile) {
+    const int sidx = tile % NST;
+    const int64_t row0 = r0 + (int64_t)tile * TRB;
+    const int tr = (int)((r1 - row0) < TRB ? (r1 - row0) : TRB);
+    T* Qs = stage0 + sidx * stage_elems;
+    T* Ss = Qs + (int64_t)TRB * np;
+    T* gs = Ss + (int64_t)TRB * GK;
+    const uint32_t bq = (uint32_t)(tr * np * sizeof(T)), bs = (uint32_t)(tr * GK * sizeof(T));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[sidx], bq + bs + (alpha ? bs : 0u));
+    tma_load_1d(Qs, Q + row0 * np, bq, &full[sidx]);
+    tma_load_1d(Ss, S + row0 * GK, bs, &full[sidx]);
+    if (alpha) tma_load_1d(gs, g + row0 * GK, bs, &full[sidx]);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < ntiles; ++issued) issue(issued);
+  T cs = 0;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int sidx = tile % NST;
+    if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
+      abort_s = 1;
+      atomicExch(st.err, 1);
+    }
+    __syncthreads();
+    if (abort_s) {
+      if (tid == 0) tma_drain(full, NST, tile + 1, issued);
+      return;
+    }
+    const int64_t row0 = r0 + (int64_t)tile * TRB;
+    const int tr = (int)((r1 - row0) < TRB ? (r1 - row0) : TRB);
+    const T* Qs = stage0 + sidx * stage_elems;
+    const T* Ss = Qs + (int64_t)TRB * np;
+    const T* gs = Ss + (int64_t)TRB * GK;
+    // part[(r*JJ + jj)*nqp + q]: consecutive threads write consecutive words,
+    // and the readers below (consecutive jj) hit distinct banks (nqp % 32 == 1)
+    if (tid < nq) {
+      for (int r = 0; r < tr; ++r) {
+        T qv[4];
+        Vec4<T>::load(Qs + (int64_t)r * np + 4 * tid, qv);
+        T* dst = part + (int64_t)r * JJ * nqp + tid;
+#pragma unroll
+        for (int jj = 0; jj < JJ; ++jj) {
+          T acc = qv[0] * creg[0][jj];
+#pragma unroll
+          for (int c = 1; c < 4; ++c) acc += qv[c] * creg[c][jj];
+          dst[(int64_t)jj * nqp] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    const int nout = tr * G * JJ;
+    for (int o = tid; o < nout; o += blockDim.x) {
+      const int jj = o % JJ, rest = o / JJ, i = rest % G, r = rest / G;
+      const int qa = __ldg(poff + i) >> 2, qb = __ldg(poff + i + 1) >> 2;
+      T sum = 0;
+      const T* pr = part + (int64_t)(r * JJ + jj) * nqp;
+      for (int qq = qa; qq < qb; ++qq) sum += pr[qq];
+      const T gold = alpha ? gs[o] : (T)0;
+      const T gn = gold - lam_s[jj] * (Ss[o] - sum);
+      g[row0 * GK + o] = gn;
+      cs += gn * gn;
+    }
+    __syncthreads();
+    if (tid == 0 && issued < ntiles) issue(issued++);
+  }
+  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
+}
+
+// Projection update, "block x column" form (TMA-streamed, JJ == k, n_i <= 32):
+// thread = (block i, right-hand side jj) [x row group], holding C[c, jj] of
+// its block's columns in registers; per row it forms
+//   t = S[t, i, jj] - sum_{c in block i} Q[t, c] C[c, jj]
+// directly (no partial buffer, one barrier pair per tile), reading Q from the
+// staged tile with 16-byte loads that all threads of a block share.
+template <typename T, int JJ, int NP>
+__global__ void __launch_bounds__(512, 1)
+k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict__ Q, const T* __restrict__ S,
+                 T* __restrict__ g, const T* __restrict__ C, const int* __restrict__ poff, int alpha,
+                 const double* __restrict__ lam, double lam_const, double* __restrict__ cpart, PcgState st,
+                 int use_state) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+  T* stage0 = reinterpret_cast<T*>(smraw + 128);
+  const int64_t GK = (int64_t)G * JJ;
+  const int64_t stage_elems = (int64_t)TRB * (np + (alpha ? 2 : 1) * GK);
+  __shared__ double red[16 * 16];
+  __shared__ T lam_s[JJ];
+  __shared__ int abort_s;
+  const int tid = threadIdx.x;
+  if (*st.err) return;
+  if (use_state) {
+    const int slot = (*st.it - 1) & 1;
+    int any = 0;
+    for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jj];
+    if (!any) {
+      if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = 0.0;
+      return;
+    }
+  }
+  if (tid < JJ) lam_s[tid] = (T)(lam ? lam[tid] : lam_const);
+  const int npairs = G * JJ;
+  const int nrg = npairs >= (int)blockDim.x ? 1 : (int)blockDim.x / npairs;
+  const int rg = tid / (npairs < (int)blockDim.x ? npairs : (int)blockDim.x);
+  const bool busy = rg < nrg;
+  // the pairs of this thread, their quad ranges and C values
+  int pc0[NP], nqi[NP], jjp[NP], ip[NP];
+  bool has[NP];
+  T creg[NP][8][4];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const int pr = (npairs < (int)blockDim.x ? tid % npairs : tid) + a * blockDim.x;
+    has[a] = busy && pr < npairs;
+    const int i = has[a] ? pr / JJ : 0, jj = pr % JJ;
+    ip[a] = i;
+    jjp[a] = jj;
+    pc0[a] = has[a] ? poff[i] : 0;
+    nqi[a] = has[a] ? (poff[i + 1] - poff[i]) >> 2 : 0;
+#pragma unroll
+    for (int qq = 0; qq < 8; ++qq)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        creg[a][qq][c] = (qq < nqi[a]) ? C[(int64_t)(pc0[a] + 4 * qq + c) * JJ + jj] : (T)0;
+  }
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int ntiles = (int)((r1 - r0 + TRB - 1) / TRB);
+  if (tid == 0) {
+    for (int q = 0; q < NST; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int tile) {
+    const int sidx = tile % NST;
+    const int64_t row0 = r0 + (int64_t)tile * TRB;
+    const int tr = (int)((r1 - row0) < TRB ? (r1 - row0) : TRB);
+    T* Qs = stage0 + sidx * stage_elems;
+    T* Ss = Qs + (int64_t)TRB * np;
+    T* gs = Ss + (int64_t)TRB * GK;
+    const uint32_t bq = (uint32_t)(tr * np * sizeof(T)), bs = (uint32_t)(tr * GK * sizeof(T));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[sidx], bq + bs + (alpha ? bs : 0u));
+    tma_load_1d(Qs, Q + row0 * np, bq, &full[sidx]);
+    tma_load_1d(Ss, S + row0 * GK, bs, &full[sidx]);
+    if (alpha) tma_load_1d(gs, g + row0 * GK, bs, &full[sidx]);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < ntiles; ++issued) issue(issued);
+  T cs = 0;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int sidx = tile % NST;
+    if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
+      abort_s = 1;
+      atomicExch(st.err, 1);
+    }
+    __syncthreads();
+    if (abort_s) {
+      if (tid == 0) tma_drain(full, NST, tile + 1, issued);
+      return;
+    }
+    const int64_t row0 = r0 + (int64_t)tile * TRB;
+    const int tr = (int)((r1 - row0) < TRB ? (r1 - row0) : TRB);
+    const T* Qs = stage0 + sidx * stage_elems;
+    const T* Ss = Qs + (int64_t)TRB * np;
+    const T* gs = Ss + (int64_t)TRB * GK;
+    for (int r = rg; r < tr; r += nrg) {
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (has[a]) {
+          const T* qrow = Qs + (int64_t)r * np + pc0[a];
+          T sum = 0;
+#pragma unroll
+          for (int qq = 0; qq < 8; ++qq) {
+            if (qq < nqi[a]) {
+              T qv[4];
+              Vec4<T>::load(qrow + 4 * qq, qv);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) sum += qv[c] * creg[a][qq][c];
+            }
+          }
+          const int64_t o = (int64_t)r * GK + (int64_t)ip[a] * JJ + jjp[a];
+          const T gold = alpha ? gs[o] : (T)0;
+          const T gn = gold - lam_s[jjp[a]] * (Ss[o] - sum);
+          g[row0 * GK + o] = gn;
+          cs += gn * gn;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && issued < ntiles) issue(issued++);
+  }
+  // per-column sums: thread's columns are jjp[a]; with npairs a multiple of JJ
+  // and blockDim a multiple of JJ every thread's jj is tid % JJ
+  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
+}
+
+template <typename T, int JJ, int RI>
+__global__ void __launch_bounds__(512, 1)
+k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict__ Om, const T* __restrict__ g,
+                 T* __restrict__ u, T* __restrict__ w, T* __restrict__ S, T* __restrict__ wbest, PcgState st,
+                 const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+  T* Om_s = reinterpret_cast<T*>(smraw + 128);
+  T* stage0 = Om_s + (int64_t)G * Gq;
+  const int64_t GK = (int64_t)G * JJ;
+  const int64_t stage_elems = (int64_t)TR * 3 * GK;
+  __shared__ double red[16 * 16];
+  __shared__ double mu_s[JJ], lamp_s[JJ];
+  __shared__ int act_s[JJ], snap_s[JJ], anyp_s, abort_s;
+  const int tid = threadIdx.x;
+  if (*st.err) return;   // an earlier bounded wait gave up: the run is being abandoned
+  if (tid == 0) anyp_s = 0;
+  const double csum = sum_partials<JJ>(cpart, ncpart, JJ, 0, red);
+  if (tid < JJ) {
+    const StepScalars sc = step_prologue(st, tid, JJ, csum, blockIdx.x == 0);
+    mu_s[tid] = sc.mu;
+    lamp_s[tid] = sc.lam_prev;
+    act_s[tid] = sc.act;
+    snap_s[tid] = sc.snap;
+    if (sc.act_prev) atomicOr(&anyp_s, 1);
+  }
+  __syncthreads();
+  if (!anyp_s) return;   // every column already stopped: nothing changes
+  for (int64_t e = tid; e < (int64_t)G * Gq; e += blockDim.x) Om_s[e] = Om[e];
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int ntiles = (int)((r1 - r0 + TR - 1) / TR);
+  if (tid == 0) {
+    for (int q = 0; q < NST; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int tile) {
+    const int sidx = tile % NST;
+    const int64_t row0 = r0 + (int64_t)tile * TR;
+    const int tr = (int)((r1 - row0) < TR ? (r1 - row0) : TR);
+    T* gs = stage0 + sidx * stage_elems;
+    const uint32_t bs = (uint32_t)(tr * GK * sizeof(T));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[sidx], 3 * bs);
+    tma_load_1d(gs, g + row0 * GK, bs, &full[sidx]);
+    tma_load_1d(gs + (int64_t)TR * GK, u + row0 * GK, bs, &full[sidx]);
+    tma_load_1d(gs + (int64_t)2 * TR * GK, w + row0 * GK, bs, &full[sidx]);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < ntiles; ++issued) issue(issued);
+  const int nhq = Gq >> 2;
+  const int jj_t = tid % JJ;
+  double dsum = 0.0;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int sidx = tile % NST;
+    if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
+      abort_s = 1;
+      atomicExch(st.err, 1);
+    }
+    __syncthreads();
+    if (abort_s) {
+      if (tid == 0) tma_drain(full, NST, tile + 1, issued);
+      return;
+    }
+    const int64_t row0 = r0 + (int64_t)tile * TR;
+    const int tr = (int)((r1 - row0) < TR ? (r1 - row0) : TR);
+    const T* gs = stage0 + sidx * stage_elems;
+    T* us = const_cast<T*>(gs) + (int64_t)TR * GK;
+    const T* ws = gs + (int64_t)2 * TR * GK;
+    // elementwise (contiguous tile): w -= lam_prev u_old ; u = g + mu u_old
+    const int ne = tr * (int)GK;
+    for (int e = tid; e < ne; e += blockDim.x) {
+      const int jj = e % JJ;
+      const T uo = us[e];
+      const T lp = (T)lamp_s[jj];
+      const T wn = ws[e] - lp * uo;
+      if (lp != (T)0) w[row0 * GK + e] = wn;
+      if (snap_s[jj]) wbest[row0 * GK + e] = wn;
+      if (act_s[jj]) {
+        const T un = gs[e] + (T)mu_s[jj] * uo;
+        u[row0 * GK + e] = un;
+        us[e] = un;
+      }
+    }
+    __syncthreads();
+    // S = U Omega: item = (RI-row group, h quad, jj), RI x 4 outputs per item
+    const int ngrp = (tr + RI - 1) / RI;
+    const int nitems = ngrp * nhq * JJ;
+    T dloc = 0;
+    for (int itm = tid; itm < nitems; itm += blockDim.x) {
+      const int rest = itm / JJ;
+      const int hq = rest % nhq, tg = rest / nhq;
+      const T* ur[RI];
+#pragma unroll
+      for (int a = 0; a < RI; ++a) {
+        const int t = RI * tg + a;
+        ur[a] = us + (int64_t)(t < tr ? t : RI * tg) * GK + jj_t;
+      }
+      T acc[RI][4];
+#pragma unroll
+      for (int a = 0; a < RI; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0;
+      for (int gg = 0; gg < G; ++gg) {
+        T om[4];
+        Vec4<T>::load(Om_s + (int64_t)gg * Gq + 4 * hq, om);
+#pragma unroll
+        for (int a = 0; a < RI; ++a) {
+          const T v = ur[a][gg * JJ];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] += v * om[c];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < RI; ++a) {
+        const int t = RI * tg + a;
+        if (t < tr) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int h = 4 * hq + c;
+            if (h < G) {
+              S[(row0 + t) * GK + h * JJ + jj_t] = acc[a][c];
+              dloc += acc[a][c] * ur[a][h * JJ];
+            }
+          }
+        }
+      }
+    }
+    dsum += (double)dloc;
+    __syncthreads();
+    if (tid == 0 && issued < ntiles) issue(issued++);
+  }
+  const double d = reduce_cols_strided<JJ>(dsum, red);
+  if (tid < JJ) dpart[(int64_t)blockIdx.x * JJ + tid] = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -764,6 +1161,16 @@ __global__ void k_unpad_q(int64_t M, int G, int np, const int* __restrict__ off,
 template <typename T, int JJ>
 static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S,
                                  T* wbest, const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
+  if (p.tma_sigma) {
+#define SIG_(R)                                                                                                  \
+  k_sigma_step_tma<T, JJ, R><<<p.n_sigma, 512, p.sigma_tma_smem, s>>>(gm.M, gm.G, gm.Gq, p.tr_tma, p.nst_sigma, Om, \
+                                                                       g, u, w, S, wbest, st, cpart, p.n_cpart, dpart)
+    if (p.ri == 4) SIG_(4);
+    else if (p.ri == 2) SIG_(2);
+    else SIG_(1);
+#undef SIG_
+    return;
+  }
   dim3 grid(p.n_sigma, 1, k / JJ);
   const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
   k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, wbest, st, cpart,
@@ -792,8 +1199,25 @@ template <typename T, int JJ>
 static void launch_proj_update_jj(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g,
                                   const T* C, int alpha, const double* lam, double lam_const, double* cpart,
                                   const PcgState& st, int use_state, cudaStream_t s) {
+  if (p.bj_update) {
+    if (p.bj_np == 2)
+      k_proj_update_bj<T, JJ, 2><<<p.n_update, 512, p.bj_smem, s>>>(gm.M, gm.G, gm.np, p.trb_bj, p.nst_bj, Q, S, g,
+                                                                     C, gm.d_poff, alpha, lam, lam_const, cpart, st,
+                                                                     use_state);
+    else
+      k_proj_update_bj<T, JJ, 1><<<p.n_update, 512, p.bj_smem, s>>>(gm.M, gm.G, gm.np, p.trb_bj, p.nst_bj, Q, S, g,
+                                                                     C, gm.d_poff, alpha, lam, lam_const, cpart, st,
+                                                                     use_state);
+    return;
+  }
+  if (p.tma_update) {
+    k_proj_update_tma<T, JJ><<<p.n_update, p.update_threads, p.update_tma_smem, s>>>(
+        gm.M, gm.G, gm.np, gm.nq, p.trb_tma, p.nst_update, Q, S, g, C, gm.d_poff, alpha, lam, lam_const, cpart, st,
+        use_state);
+    return;
+  }
   dim3 grid(p.n_update, p.n_ugroups, k / JJ);
-  const size_t smem = sizeof(T) * (size_t)p.TRB * p.ug_max_quads * JJ;
+  const size_t smem = p.update_smem;
   k_proj_update<T, JJ><<<grid, p.ug_threads, smem, s>>>(gm.M, gm.G, gm.np, k, p.TRB, Q, S, g, C, gm.d_poff,
                                                          gm.d_ug_blk0, alpha, lam, lam_const, cpart, st, use_state);
 }
@@ -946,6 +1370,30 @@ template void launch_layout_to_colmajor<double>(const Geom&, int, const double*,
 template void launch_convert<double, float>(int64_t, const double*, float*, double, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);
 template void launch_colsumsq<double>(const IterPlan&, const Geom&, int, const double*, double*, cudaStream_t);
+template <typename T>
+cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes) {
+  cudaError_t e = cudaSuccess;
+#define C_(J)                                                                                                      \
+  e = cudaFuncSetAttribute(k_sigma_step_tma<T, J, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sigma_bytes); \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_sigma_step_tma<T, J, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                             (int)sigma_bytes);                                                                    \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_sigma_step_tma<T, J, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                             (int)sigma_bytes);                                                                    \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_proj_update_tma<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                             (int)update_bytes);                                                                   \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_proj_update_bj<T, J, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bj_bytes); \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_proj_update_bj<T, J, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bj_bytes);
+  GS_DISPATCH_JJ(JJ, C_)
+#undef C_
+  return e;
+}
+template cudaError_t set_tma_smem_attrs<double>(int, size_t, size_t, size_t);
+template cudaError_t set_tma_smem_attrs<float>(int, size_t, size_t, size_t);
 template cudaError_t set_smem_attrs<double>(int, size_t, size_t);
 template cudaError_t set_smem_attrs<float>(int, size_t, size_t);
 

@@ -24,6 +24,14 @@ struct IterPlan {
   int TRB = 1;             // rows per proj_update tile
   size_t sigma_smem = 0;
   size_t update_smem = 0;
+  // TMA-streamed kernels (used when JJ == k and rows are 16-byte multiples)
+  bool tma_sigma = false, tma_update = false;
+  int tr_tma = 1, nst_sigma = 3, trb_tma = 1, nst_update = 3, update_threads = 256;
+  int ri = 4;              // rows per Sigma-apply item of the TMA step
+  size_t sigma_tma_smem = 0, update_tma_smem = 0;
+  bool bj_update = false;  // block x column projection update (n_i <= 32, G*k <= 1024)
+  int bj_np = 1, trb_bj = 1, nst_bj = 3;
+  size_t bj_smem = 0;
 };
 
 template <typename T>
@@ -67,5 +75,7 @@ void launch_shift_diag(int G, int Gq, const double* Om64, float* Om32, double re
 void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, cudaStream_t s);
 template <typename T>
 cudaError_t set_smem_attrs(int JJ, size_t bytes, size_t upd_bytes);
+template <typename T>
+cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes);
 
 }  // namespace glmsur

@@ -31,7 +31,7 @@ class GlmSur:
 
     def __init__(self, X_blocks, Omega, precision: str = "fp64", tol: float = 1e-13, maxit: int = 0,
                  stagnation_window: int = 25, inner_tol: float = 1e-5, max_refine: int = 8,
-                 chunk: int = 16, inner_shift: float = 1e-6, device="cuda"):
+                 chunk: int = 16, inner_shift: float = 0.0, device="cuda"):
         self.device = torch.device(device)
         blocks = [_dev_f64(x, self.device) for x in X_blocks]
         self.n_i = [int(x.shape[1]) for x in blocks]
