@@ -147,6 +147,38 @@ def oracle_iters_per_solve():
     return None, None
 
 
+def aggregate(ms_local, pg, world, device="cpu"):
+    """Replicas: the job's time per step is the slowest rank's; the job's
+    throughput is every rank's solve over that time."""
+    ms = ms_local
+    if pg is not None:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * 1e3 / ms
+
+
+NCU_SECTION = {"sigma_step": "k_sigma_step_tma", "proj_partial": "k_proj_partial", "proj_update": "k_proj_update_bj"}
+
+
+def ncu_traffic(args, kernel):
+    """DRAM bytes per launch of `kernel` from the committed Nsight Compute
+    summary of this workload (float32 bulk only), else None."""
+    if args.precision != "fp32_refine" or kernel not in NCU_SECTION:
+        return None
+    path = os.path.join(ROOT, "profiles", f"step_kernels_sur-singular-g{args.G}-m{args.M}-k{args.k}.md")
+    if not os.path.exists(path):
+        return None
+    cur = None
+    for line in open(path):
+        if line.startswith("## "):
+            cur = line[3:].split("<")[0].strip()
+        elif line.startswith("traffic_bytes_per_launch:") and cur == NCU_SECTION[kernel]:
+            return int(line.split(":")[1])
+    return None
+
+
 def run_reference(args, rank, world, pg):
     """CPU reference arm: the oracle's float64 PCG timed on the host cores."""
     if rank != 0:
@@ -229,11 +261,7 @@ def run_ours(args, rank, world, local, pg):
         pg.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = L.glm_sur_launch_count(h.handle) - launches0
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1e3 / ms
+    ms, value = aggregate(ms, pg, world, dev)
 
     # ---- end to end through the public API with host buffers
     Y_host = torch.as_tensor(p.Y.T.copy()).pin_memory()
@@ -277,13 +305,7 @@ def run_ours(args, rank, world, local, pg):
     ach = kbytes[dname] / (prof[dom] * 1e-3) / 1e9
     b_iter = 2 * pb * M * n + 8 * pb * mk
     ach_iter = b_iter / (prof[4] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(f"{dname}:{args.precision}:k{k}")
-        except Exception:
-            traffic = None
+    traffic = ncu_traffic(args, dname)
 
     # ---- float64 PCG on the same workload (comparison at the same accuracy)
     fp64 = None
