@@ -160,6 +160,31 @@ int64_t glm_sur_launch_count(glm_sur_t h);
  * fails until the next solve). */
 glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_stream_t stream);
 
+/*
+ * glm_sur_ols_static -- per-block least squares b_i = R_i^-1 Q_i^T y_i
+ * (the ordinary least-squares estimate of every equation, from the factors
+ * the handle already holds), for callers that must not allocate device
+ * memory: code whose device memory is owned by another allocator or fully
+ * reserved up front, or that must not trigger the implicit synchronisation
+ * a cudaMalloc/cudaFree can cause.  It allocates nothing: its intermediate
+ * sums live in one fixed 4 MiB device array inside the library (every GPU
+ * that loads the library keeps it until the process exits).  There is no
+ * counterpart in the paper; it is a service of this library.
+ *
+ *   Y  : DEVICE, m x k column-major (m = G*M, column j = vec(Y_j)), ldy >= m.
+ *   b  : DEVICE output, n x k column-major, ldb >= n.
+ * Limit: (n' * k) * 2 <= 524288 doubles, n' = sum_i 4*ceil(n_i/4); larger
+ * requests return GLM_SUR_INVALID_ARG before any device work.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that may
+ * run at the same time on the GPU (different streams without ordering)
+ * race and must be serialised by the caller.  Nothing in the array needs
+ * clearing between calls: each call writes every entry it reads.
+ */
+glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int k,
+                                  double* b, int64_t ldb, glm_sur_stream_t stream);
+
 void glm_sur_destroy(glm_sur_t h);
 const char* glm_sur_status_string(glm_sur_status s);
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
     "glm_sur_destroy": (None, [_VP]),
     "glm_sur_launch_count": (ctypes.c_int64, [_VP]),
+    "glm_sur_ols_static": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP]),
     "glm_sur_profile_steps": (_I, [_VP, _I, ctypes.POINTER(_D), _VP]),
     "glm_sur_status_string": (ctypes.c_char_p, [_I]),
     "glm_sur_version": (ctypes.c_char_p, []),
@@ -144,6 +145,13 @@ def glm_sur_profile_steps(h: int, reps: int, stream: int):
     ms = (ctypes.c_double * 5)()
     check(lib().glm_sur_profile_steps(h, reps, ms, stream), "glm_sur_profile_steps")
     return [float(v) for v in ms]
+
+
+def glm_sur_ols_static(h: int, Y_ptr: int, ldy: int, k: int, b_ptr: int, ldb: int, stream: int) -> int:
+    """Per-block least squares from the handle's factors without allocating
+    device memory; returns the status code (GLM_SUR_INVALID_ARG when the
+    request exceeds the library's fixed scratch array)."""
+    return int(lib().glm_sur_ols_static(h, Y_ptr, ldy, k, b_ptr, ldb, stream))
 
 
 def glm_sur_destroy(h: int) -> None:

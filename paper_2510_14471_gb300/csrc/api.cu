@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "glm_sur.h"
 #include "internal.h"
+#include "noalloc.h"
 #include "pcg.h"
 
 namespace glmsur {
@@ -857,6 +858,15 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
   h->has_w = false;
   h->graph.reset();   // the captured graph baked the previous tolerance
   return rc;
+}
+
+glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb,
+                                  glm_sur_stream_t stream) {
+  if (!h || !Y || !b || k < 1 || k > kMaxRhs) return GLM_SUR_INVALID_ARG;
+  const Geom& gm = h->gm;
+  if (ldy < gm.M * gm.G || ldb < gm.n) return GLM_SUR_INVALID_ARG;
+  if ((long long)gm.np * k * 2 > kOlsScratchDoubles) return GLM_SUR_INVALID_ARG;
+  return ols_static(gm, h->Q64, h->R, Y, ldy, k, b, ldb, h->sms, reinterpret_cast<cudaStream_t>(stream));
 }
 
 void glm_sur_destroy(glm_sur_t h) {
