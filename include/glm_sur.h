@@ -132,6 +132,34 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k,
                              double* b, int64_t ldb, int* iters, double* relres,
                              glm_sur_stream_t stream);
 
+/*
+ * glm_sur_set_restrictions -- linear restrictions C b = d on the parameters
+ * (Sec. 5.1): the model becomes the GLM of eq. (RGLM1setup) with
+ * Sigma_aug = diag(Omega (x) I_M, 0), X_aug = [(+)X_i; C], y_aug = [y; d],
+ * and the preconditioner of eq. (invprec) with D = I, whose X* and Pi are
+ * those of eq. (rglm1m): N = X_aug^T X_aug = (+)R_i^T R_i + C^T C is formed
+ * and inverted once here (float64 Cholesky).
+ *   C  : DEVICE, kc x n column-major, ldc >= kc (copied).  kc = 0 removes
+ *        the restrictions.  n <= 25600.
+ * A singular N (the restrictions and the X_i do not determine b) is reported
+ * by glm_sur_get_setup_status as GLM_SUR_RANK_DEFICIENT.  Restricted solves
+ * run in float64 (FP32_REFINE returns GLM_SUR_INVALID_ARG).
+ */
+glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ldc, int kc,
+                                        glm_sur_stream_t stream);
+
+/*
+ * glm_sur_solve_restricted -- glm_sur_solve for a handle with restrictions:
+ * Algorithm glmpcg2 on the restricted GLM (at most m + kc - n + 1 steps in
+ * exact arithmetic, Sec. 5.1), b = X*^T (y_aug - Sigma_aug w).
+ *   d  : DEVICE, kc x k column-major, ldd >= kc; NULL means d = 0.
+ * Other arguments as glm_sur_solve.  (glm_sur_solve on a restricted handle
+ * solves with d = 0.)
+ */
+glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ldy, const double* d,
+                                        int64_t ldd, int k, double* b, int64_t ldb, int* iters,
+                                        double* relres, glm_sur_stream_t stream);
+
 /* Synchronises and copies the per-column status of the last solve (k values,
  * glm_sur_status codes) into the HOST array `status`. */
 glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k);

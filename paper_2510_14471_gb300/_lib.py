@@ -48,6 +48,8 @@ SIGNATURES = {
     "glm_sur_set_opts": (_I, [_VP, ctypes.POINTER(GlmSurOpts)]),
     "glm_sur_solve": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_get_status": (_I, [_VP, ctypes.POINTER(_I), _I]),
+    "glm_sur_set_restrictions": (_I, [_VP, _VP, _I64, _I, _VP]),
+    "glm_sur_solve_restricted": (_I, [_VP, _VP, _I64, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_get_w": (_I, [_VP, _VP, _I64, _VP]),
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
     "glm_sur_destroy": (None, [_VP]),
@@ -119,6 +121,16 @@ def glm_sur_set_opts(h: int, opts: GlmSurOpts) -> None:
 def glm_sur_solve(h: int, Y_ptr: int, ldy: int, k: int, b_ptr: int, ldb: int, iters_ptr: int,
                   relres_ptr: int, stream: int) -> None:
     check(lib().glm_sur_solve(h, Y_ptr, ldy, k, b_ptr, ldb, iters_ptr, relres_ptr, stream), "glm_sur_solve")
+
+
+def glm_sur_set_restrictions(h: int, C_ptr: int, ldc: int, kc: int, stream: int) -> None:
+    check(lib().glm_sur_set_restrictions(h, C_ptr, ldc, kc, stream), "glm_sur_set_restrictions")
+
+
+def glm_sur_solve_restricted(h: int, Y_ptr: int, ldy: int, d_ptr: int, ldd: int, k: int, b_ptr: int, ldb: int,
+                             iters_ptr: int, relres_ptr: int, stream: int) -> None:
+    check(lib().glm_sur_solve_restricted(h, Y_ptr, ldy, d_ptr, ldd, k, b_ptr, ldb, iters_ptr, relres_ptr, stream),
+          "glm_sur_solve_restricted")
 
 
 def glm_sur_get_status(h: int, k: int):

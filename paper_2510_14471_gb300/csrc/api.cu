@@ -16,6 +16,7 @@
 #include "internal.h"
 #include "noalloc.h"
 #include "pcg.h"
+#include "rglm.h"
 
 namespace glmsur {
 
@@ -94,6 +95,15 @@ struct glm_sur_ctx {
   int plan_k = -1, plan_prec = -1;
   bool has_w = false;
   int64_t launches = 0;        // kernel launches issued (graph nodes included)
+  // linear restrictions C b = d (Sec. 5.1)
+  int kc = 0;
+  double* Cmat = nullptr;      // kc x n column-major (ld = kc)
+  double* Nmat = nullptr;      // n x n: X_aug^T X_aug, then its Cholesky factor
+  double* Minv = nullptr;      // n x n: (X_aug^T X_aug)^-1
+  double* cbuf = nullptr;      // n x k coefficients c = N^-1 a
+  double* fbuf = nullptr;      // n' x k f_i = R_i c_i
+  double* gC = nullptr;        // kc x k restriction rows of g
+  int rcap = 0;                // k capacity of cbuf / fbuf / gC
 };
 
 namespace {
@@ -138,6 +148,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   p.ug_threads = (int)std::min<int64_t>(512, ceil_div(gm.ug_max_quads, 32) * 32);
   p.n_update = (int)std::max<int64_t>(1, std::min<int64_t>(gm.M, ceil_div(target, (int64_t)njg * p.n_ugroups)));
   p.n_cpart = p.n_update * p.n_ugroups;
+  p.extra_cpart = h->kc > 0 ? 1 : 0;
   const size_t upd_row = sz * (size_t)(gm.ug_max_quads + 32) * p.JJ;   // padded quad stride
   p.TRB = (int)std::max<size_t>(2, std::min<size_t>(32, (48 * 1024) / upd_row));
   p.update_smem = (size_t)p.TRB * upd_row;
@@ -195,6 +206,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
       p.n_update = h->sms;
       p.n_cpart = h->sms;
     }
+    p.extra_cpart = h->kc > 0 ? 1 : 0;
   }
   cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem, p.update_smem)
                             : set_smem_attrs<float>(p.JJ, p.sigma_smem, p.update_smem);
@@ -335,7 +347,15 @@ void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
                          Bufs<T>::wb(h), h->st, h->cpart, h->dpart, s);
     launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Cpart, h->st, 1, s);
     launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
-    launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Bufs<T>::g(h), C, 1, h->st.lam, 0.0,
+    const T* Cupd = C;
+    if (h->kc > 0 && sizeof(T) == sizeof(double)) {
+      // restricted GLM (Sec. 5.1): c = N^-1 [R_i^T e_i], f_i = R_i c_i, g_C += lambda C c
+      rglm_coef(h->gm, k, reinterpret_cast<const double*>(C), h->R, h->Minv, h->Cmat, h->kc, h->kc, nullptr, 0, 0.0,
+                h->cbuf, h->fbuf, nullptr, 0, s);
+      rglm_gc(h->gm, k, h->kc, h->Cmat, h->kc, h->cbuf, nullptr, 0, h->st.lam, 0, h->gC, h->cpart, p.n_cpart, s);
+      Cupd = reinterpret_cast<const T*>(h->fbuf);
+    }
+    launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Bufs<T>::g(h), Cupd, 1, h->st.lam, 0.0,
                           h->cpart, h->st, 1, s);
   }
 }
@@ -365,7 +385,7 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
   const int64_t max_launch = (int64_t)maxit / chunk + 3;
   for (int64_t c = 0; c < max_launch; ++c) {
     GS_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
-    h->launches += 4 * (int64_t)chunk;
+    h->launches += (h->kc > 0 ? 6 : 4) * (int64_t)chunk;
     // done flag and error word side by side: h_done[2*slot], h_done[2*slot + 1]
     GS_CUDA_TRY(cudaMemcpyAsync(&h->h_done[2 * (c & 1)], h->st.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA_TRY(cudaEventRecord(h->ev[c & 1], s));
@@ -382,16 +402,31 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
 }
 
 // g = -P y  (first residual of the PCG started at w = 0), u = w = 0, partials of g^T g.
+// Restricted (d != null or kc > 0): g = -Pi y_aug, y_aug = [y; d] (Sec. 5.1).
 template <typename T>
-glm_sur_status pcg_init(glm_sur_ctx* h, int k, const T* y_layout, cudaStream_t s) {
+glm_sur_status pcg_init(glm_sur_ctx* h, int k, const T* y_layout, cudaStream_t s, const double* d = nullptr,
+                        int64_t ldd = 0) {
   const IterPlan& p = h->plan;
   T* Cpart = reinterpret_cast<T*>(h->Cpart);
   T* C = reinterpret_cast<T*>(h->Cfin);
   const size_t mk = (size_t)h->gm.M * h->gm.G * k;
   launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), y_layout, Cpart, h->st, 0, s);
   launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 0, nullptr, s);
-  launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), y_layout, Bufs<T>::g(h), C, 0, nullptr, 1.0, h->cpart, h->st, 0,
-                        s);
+  const T* Cupd = C;
+  if (h->kc > 0 && sizeof(T) == sizeof(double)) {
+    GS_CUDA_TRY(rglm_coef(h->gm, k, reinterpret_cast<const double*>(C), h->R, h->Minv, h->Cmat, h->kc, h->kc, d, ldd,
+                          1.0, h->cbuf, h->fbuf, nullptr, 0, s));
+    Cupd = reinterpret_cast<const T*>(h->fbuf);
+  }
+  launch_proj_update<T>(p, h->gm, k, Bufs<T>::Q(h), y_layout, Bufs<T>::g(h), Cupd, 0, nullptr, 1.0, h->cpart, h->st,
+                        0, s);
+  if (h->kc > 0 && sizeof(T) == sizeof(double)) {
+    if (d == nullptr) GS_CUDA_TRY(cudaMemsetAsync(h->gC, 0, sizeof(double) * (size_t)h->kc * k, s));
+    // g_C = C c - d (d = 0 when not given)
+    GS_CUDA_TRY(rglm_gc(h->gm, k, h->kc, h->Cmat, h->kc, h->cbuf, d, ldd, nullptr, d ? 1 : 2, h->gC, h->cpart,
+                        p.n_cpart, s));
+    h->launches += 2;
+  }
   h->launches += 3;
   GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::u(h), 0, mk * sizeof(T), s));
   GS_CUDA_TRY(cudaMemsetAsync(Bufs<T>::w(h), 0, mk * sizeof(T), s));
@@ -424,12 +459,20 @@ glm_sur_status project_correction(glm_sur_ctx* h, int k, const IterPlan& p64, cu
   return GLM_SUR_OK;
 }
 
-// b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 5.3)
-glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, int64_t ldb, cudaStream_t s) {
+// b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 5.3);
+// restricted: b = N^-1 ([R_i^T Q_i^T (y - Sigma w)_i] + C^T d)  (eq. rglm1m)
+glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, int64_t ldb, cudaStream_t s,
+                         const double* d = nullptr, int64_t ldd = 0) {
   double* Cpart = reinterpret_cast<double*>(h->Cpart);
   launch_sigma_resid<double>(p64, h->gm, k, h->Om64, h->y64, h->w64, h->E64, s);
   launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
   launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  if (h->kc > 0) {
+    GS_CUDA_TRY(rglm_coef(h->gm, k, h->C64, h->R, h->Minv, h->Cmat, h->kc, h->kc, d, ldd, 1.0, h->cbuf, h->fbuf, b,
+                          ldb, s));
+    h->launches += 4;
+    return GLM_SUR_OK;
+  }
   launch_tri_solve(h->gm, k, h->R, h->C64, b, ldb, s);
   h->launches += 4;
   GS_CUDA_TRY(cudaGetLastError());
@@ -553,6 +596,13 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   SETUP_TRY(dalloc(&gm.d_quad_blk, gm.nq));
   SETUP_TRY(dalloc(&gm.d_r_off, G + 1));
   SETUP_TRY(dalloc(&gm.d_ug_blk0, gm.n_ugroups + 1));
+  {
+    std::vector<int> col_blk(gm.n);
+    for (int i = 0; i < G; ++i)
+      for (int c = h->off[i]; c < h->off[i + 1]; ++c) col_blk[c] = i;
+    SETUP_TRY(dalloc(&gm.d_col_blk, gm.n));
+    SETUP_TRY(cudaMemcpy(gm.d_col_blk, col_blk.data(), gm.n * sizeof(int), cudaMemcpyHostToDevice));
+  }
   SETUP_TRY(cudaMemcpyAsync(gm.d_ug_blk0, ug_blk0.data(), (gm.n_ugroups + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   SETUP_TRY(cudaMemcpyAsync(gm.d_n_i, n_i, G * sizeof(int), cudaMemcpyHostToDevice, s));
   SETUP_TRY(cudaMemcpyAsync(gm.d_off, h->off.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -629,14 +679,31 @@ glm_sur_status glm_sur_set_opts(glm_sur_t h, const glm_sur_opts* opts) {
   return GLM_SUR_OK;
 }
 
-glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
-                             double* relres, glm_sur_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+glm_sur_status ensure_restriction_workspace(glm_sur_ctx* h, int k) {
+  if (h->kc == 0 || k <= h->rcap) return GLM_SUR_OK;
+  dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
+  h->rcap = 0;
+  GS_CUDA_TRY(dalloc(&h->cbuf, (size_t)h->gm.n * k));
+  GS_CUDA_TRY(dalloc(&h->fbuf, (size_t)h->gm.np * k));
+  GS_CUDA_TRY(dalloc(&h->gC, (size_t)h->kc * k));
+  h->rcap = k;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
+                          int64_t ldb, int* iters, double* relres, cudaStream_t s) {
   if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
   const Geom& gm = h->gm;
   const int64_t m = gm.M * gm.G;
   if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (h->kc > 0 && (h->opts.precision != GLM_SUR_PREC_FP64 || (d && ldd < h->kc))) return GLM_SUR_INVALID_ARG;
   glm_sur_status rc = ensure_workspace(h, k);
+  if (rc != GLM_SUR_OK) return rc;
+  rc = ensure_restriction_workspace(h, k);
   if (rc != GLM_SUR_OK) return rc;
   const bool fp64 = h->opts.precision == GLM_SUR_PREC_FP64;
   IterPlan p64;
@@ -661,7 +728,7 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
   if (fp64) {
     rc = reset_state(h, k, h->opts.tol, maxit, h->opts.stagnation_window, s);
     if (rc != GLM_SUR_OK) return rc;
-    rc = pcg_init<double>(h, k, h->y64, s);
+    rc = pcg_init<double>(h, k, h->y64, s, d, ldd);
     if (rc != GLM_SUR_OK) return rc;
     GS_CUDA_TRY(cudaGetLastError());
     rc = run_steps<double>(h, k, maxit, s);
@@ -744,9 +811,48 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
     GS_CUDA_TRY(cudaStreamSynchronize(s));
   }
   if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, h->d_iters_acc, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  rc = recover_b(h, k, p64, b, ldb, s);
+  rc = recover_b(h, k, p64, b, ldb, s, d, ldd);
   if (rc != GLM_SUR_OK) return rc;
   h->has_w = true;
+  return GLM_SUR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
+                             double* relres, glm_sur_stream_t stream) {
+  return solve_impl(h, Y, ldy, nullptr, 0, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
+}
+
+glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd,
+                                        int k, double* b, int64_t ldb, int* iters, double* relres,
+                                        glm_sur_stream_t stream) {
+  if (!h || h->kc == 0) return GLM_SUR_INVALID_ARG;
+  return solve_impl(h, Y, ldy, d, ldd, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
+}
+
+glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ldc, int kc, glm_sur_stream_t stream) {
+  if (!h || kc < 0 || (kc > 0 && (!C || ldc < kc))) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const Geom& gm = h->gm;
+  if (kc > 0 && (size_t)gm.n * sizeof(double) > 200 * 1024) return GLM_SUR_INVALID_ARG;   // n <= 25600
+  dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
+  h->rcap = 0;
+  h->kc = 0;
+  h->plan_k = -1;
+  h->graph.reset();
+  h->has_w = false;
+  if (kc == 0) return GLM_SUR_OK;
+  GS_CUDA_TRY(dalloc(&h->Cmat, (size_t)kc * gm.n));
+  GS_CUDA_TRY(dalloc(&h->Nmat, (size_t)gm.n * gm.n));
+  GS_CUDA_TRY(dalloc(&h->Minv, (size_t)gm.n * gm.n));
+  GS_CUDA_TRY(cudaMemcpy2DAsync(h->Cmat, kc * sizeof(double), C, ldc * sizeof(double), kc * sizeof(double), gm.n,
+                                cudaMemcpyDeviceToDevice, s));
+  GS_CUDA_TRY(rglm_factor(gm, h->R, h->Cmat, kc, kc, gm.d_col_blk, h->Nmat, h->Minv, h->setup_flags, s));
+  h->launches += 3;
+  h->kc = kc;
   return GLM_SUR_OK;
 }
 
@@ -875,7 +981,8 @@ void glm_sur_destroy(glm_sur_t h) {
   free_workspace(h);
   dfree(h->Q64); dfree(h->Q32); dfree(h->R); dfree(h->Om64); dfree(h->Om32); dfree(h->setup_flags);
   dfree(h->gm.d_n_i); dfree(h->gm.d_off); dfree(h->gm.d_poff); dfree(h->gm.d_quad_blk); dfree(h->gm.d_r_off);
-  dfree(h->gm.d_ug_blk0);
+  dfree(h->gm.d_ug_blk0); dfree(h->gm.d_col_blk);
+  dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);

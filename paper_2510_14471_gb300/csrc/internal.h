@@ -55,6 +55,7 @@ struct Geom {
   int* d_off = nullptr;      // unpadded column offsets (G+1)
   int* d_poff = nullptr;     // padded column offsets (G+1)
   int* d_quad_blk = nullptr; // block of every column quad (nq)
+  int* d_col_blk = nullptr;  // block of every (unpadded) column (n)
   int64_t* d_r_off = nullptr;
   // block groups of the projection update: runs of whole blocks with at most
   // kMaxGroupQuads column quads each; group g = blocks [ug_blk0[g], ug_blk0[g+1])

@@ -1164,7 +1164,8 @@ static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const
   if (p.tma_sigma) {
 #define SIG_(R)                                                                                                  \
   k_sigma_step_tma<T, JJ, R><<<p.n_sigma, 512, p.sigma_tma_smem, s>>>(gm.M, gm.G, gm.Gq, p.tr_tma, p.nst_sigma, Om, \
-                                                                       g, u, w, S, wbest, st, cpart, p.n_cpart, dpart)
+                                                                       g, u, w, S, wbest, st, cpart,          \
+                                                                       p.n_cpart + p.extra_cpart, dpart)
     if (p.ri == 4) SIG_(4);
     else if (p.ri == 2) SIG_(2);
     else SIG_(1);
@@ -1174,7 +1175,7 @@ static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const
   dim3 grid(p.n_sigma, 1, k / JJ);
   const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
   k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, wbest, st, cpart,
-                                              p.n_cpart, dpart);
+                                              p.n_cpart + p.extra_cpart, dpart);
 }
 
 template <typename T, int JJ>

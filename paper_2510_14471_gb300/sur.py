@@ -75,8 +75,19 @@ class GlmSur:
             setattr(self.opts, key, v)
         L.glm_sur_set_opts(self._h, self.opts)
 
-    def solve(self, Y) -> SolveResult:
-        """Y: (m, k) (column j = vec(Y_j)) or (m,).  Returns b as (n, k)."""
+    def set_restrictions(self, C) -> None:
+        """Linear restrictions C b = d (C: (kc, n)); None or an empty C removes them."""
+        if C is None or len(C) == 0:
+            L.glm_sur_set_restrictions(self._h, 0, 1, 0, self._stream())
+            self._C = None
+            return
+        Cd = _dev_f64(C, self.device)
+        self._C = Cd.t().contiguous()                  # column-major kc x n
+        L.glm_sur_set_restrictions(self._h, self._C.data_ptr(), Cd.shape[0], Cd.shape[0], self._stream())
+
+    def solve(self, Y, d=None) -> SolveResult:
+        """Y: (m, k) (column j = vec(Y_j)) or (m,); d: (kc, k) right-hand sides of
+        the restrictions (restricted handles only).  Returns b as (n, k)."""
         Y = _dev_f64(Y, self.device)
         if Y.dim() == 1:
             Y = Y[:, None]
@@ -85,8 +96,14 @@ class GlmSur:
         b = torch.empty((k, self.n), dtype=torch.float64, device=self.device)
         iters = torch.zeros(k, dtype=torch.int32, device=self.device)
         relres = torch.zeros(k, dtype=torch.float64, device=self.device)
-        L.glm_sur_solve(self._h, Ycm.data_ptr(), m, k, b.data_ptr(), self.n, iters.data_ptr(), relres.data_ptr(),
-                        self._stream())
+        if d is not None:
+            dd = _dev_f64(d, self.device).reshape(-1, k)
+            dcm = dd.t().contiguous()
+            L.glm_sur_solve_restricted(self._h, Ycm.data_ptr(), m, dcm.data_ptr(), dd.shape[0], k, b.data_ptr(),
+                                       self.n, iters.data_ptr(), relres.data_ptr(), self._stream())
+        else:
+            L.glm_sur_solve(self._h, Ycm.data_ptr(), m, k, b.data_ptr(), self.n, iters.data_ptr(),
+                            relres.data_ptr(), self._stream())
         status = L.glm_sur_get_status(self._h, k)
         return SolveResult(b.t(), iters, relres, status)
 

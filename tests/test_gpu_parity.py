@@ -181,3 +181,48 @@ def test_full_size_singular_workload_recovers_beta_true(precision, k):
     p = S.config1(k=k)
     r = gpu_solve(p, precision=precision)
     assert relcols(r["b"], p.beta) <= TOL_B, (r["status"], r["iters"])
+
+
+# ------------------------------------------------------------------ linear restrictions (Sec. 5.1)
+
+def gpu_solve_restricted(p, **kw):
+    h = _glmsur()(p.X_blocks, p.Omega, precision="fp64", **kw)
+    h.set_restrictions(p.C)
+    assert h.setup_status() == 0
+    r = h.solve(p.Y, d=p.d)
+    return dict(b=r.b.cpu().numpy(), iters=r.iters.cpu().numpy(), status=r.status, h=h)
+
+
+@pytest.mark.parametrize("G,M,n_i,k,kc,omega", [
+    (3, 50, [3, 3, 2], 2, 3, "spectrum"),
+    (4, 700, [5, 16, 3, 9], 3, 7, "chol"),
+    (5, 1031, [8, 4, 12, 6, 2], 1, 20, "wishart"),
+])
+def test_restricted_matches_oracle(G, M, n_i, k, kc, omega):
+    p = S.make_problem(G=G, M=M, n_i=n_i, k=k, seed=G * 31 + M, omega=omega, n_constraints=kc)
+    b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y, p.C, p.d)
+    r = gpu_solve_restricted(p, tol=1e-13)
+    assert all(s in (0, 4) for s in r["status"]), r["status"]
+    assert relcols(r["b"], b_ref) <= TOL_B
+    assert np.linalg.norm(p.C @ r["b"] - p.d) <= 1e-10 * np.linalg.norm(p.d)
+
+
+def test_restricted_iterations_match_reference_pcg():
+    p = S.make_problem(G=3, M=60, n_i=[3, 4, 2], k=2, seed=5, omega="chol", n_constraints=4)
+    ref = O.rglm_pcg_aug(p.X_blocks, p.Omega, p.Y, p.C, p.d, tol=1e-10)
+    r = gpu_solve_restricted(p, tol=1e-10)
+    assert np.all(np.abs(r["iters"].astype(int) - ref["iters"].astype(int)) <= 2), (r["iters"], ref["iters"])
+    assert relcols(r["b"], ref["b"]) <= TOL_B
+    # at most m + kc - n + 1 steps (Sec. 5.1)
+    assert max(r["iters"]) <= p.m + 4 - p.n + 1
+
+
+def test_restricted_full_size_workload_sampled_columns():
+    # G = 32, M = 50000, n_i = 16, C 64 x 512, k = 32: the restrictions hold
+    # for every column and two sampled columns match the structured oracle
+    p = S.config3(k=32)
+    r = gpu_solve_restricted(p)
+    assert np.max(np.linalg.norm(p.C @ r["b"] - p.d, axis=0) / np.linalg.norm(p.d, axis=0)) <= 1e-10
+    for j in (0, 31):
+        b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y[:, j:j + 1], p.C, p.d[:, j:j + 1])
+        assert relcols(r["b"][:, j:j + 1], b_ref) <= TOL_B, j
