@@ -216,6 +216,59 @@ glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int
 void glm_sur_destroy(glm_sur_t h);
 const char* glm_sur_status_string(glm_sur_status s);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent SUR instances (uneven G, M, n_i), each solved with
+ * the same method: float32 PCG-Aug steps (Algorithm glmpcg2, D = I) inside
+ * a float64 iterative-refinement loop, b = X*^T (y - Sigma w); one
+ * persistent launch for the whole batch, one CTA per instance at a time.
+ * ------------------------------------------------------------------------ */
+typedef struct glm_sur_batch_ctx* glm_sur_batch_t;
+
+/*
+ * glm_sur_batch_setup -- factor every block of every instance (TSQR).
+ *   count : number of instances.
+ *   G, M  : HOST arrays (count): equations (1..32) and observations of each.
+ *   n_i   : HOST array of sum_j G[j] block widths (1..32, <= M of the
+ *           instance), instance by instance.  Padded width per instance
+ *           n' = sum_i 4 ceil(n_i / 4) <= 512.
+ *   X     : DEVICE, the instances' [X_1 ... X_G] (M_j x n_j column-major,
+ *           ld = M_j) one after another.
+ *   Omega : DEVICE, the instances' Omega_j (G_j x G_j column-major) one after
+ *           another.
+ *   opts  : tol (float64 residual ||P(y - Sigma w)|| / ||P y||), inner_tol,
+ *           max_refine are used; may be NULL.  The float64 residual of a
+ *           refined solve settles at a few 1e-13 on instances of this size,
+ *           so a tol below that ends in GLM_SUR_NOT_CONVERGED after
+ *           max_refine refinement steps with b still at full accuracy.
+ */
+glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G, const int* M,
+                                   const int* n_i, const double* X, const double* Omega,
+                                   const glm_sur_opts* opts, glm_sur_stream_t stream);
+glm_sur_status glm_sur_batch_get_setup_status(glm_sur_batch_t h);
+
+/*
+ * glm_sur_batch_solve -- k in {1, 2, 4, 8} right-hand sides per instance.
+ *   Y      : DEVICE, the instances' m_j x k column-major blocks (m_j = G_j M_j,
+ *            ld = m_j, column c = vec(Y_c)) one after another.
+ *   b      : DEVICE output, the instances' n_j x k column-major blocks.
+ *   iters, relres : DEVICE outputs (nullable), count x k (instance-major):
+ *            float32 steps summed over refinement steps; final float64
+ *            relative residual.
+ * The first solve with a given k tunes the tile height (three timed
+ * launches, glm_sur_batch_tile reports them); later solves replay one
+ * captured launch while Y, b, iters and relres stay the same.
+ */
+glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, double* b, int* iters,
+                                   double* relres, glm_sur_stream_t stream);
+/* Synchronises; HOST status (count x k); returns the first status other than
+ * GLM_SUR_OK / GLM_SUR_STAGNATED. */
+glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status);
+/* Tile height chosen by the autotuner (0 before the first solve); tune_ms
+ * (HOST, 3, nullable) receives the timed candidates (8, 16, 32 rows). */
+int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms);
+int64_t glm_sur_batch_launch_count(glm_sur_batch_t h);
+void glm_sur_batch_destroy(glm_sur_batch_t h);
+
 /* Library build information (static string). */
 const char* glm_sur_version(void);
 

@@ -56,6 +56,14 @@ SIGNATURES = {
     "glm_sur_launch_count": (ctypes.c_int64, [_VP]),
     "glm_sur_ols_static": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP]),
     "glm_sur_profile_steps": (_I, [_VP, _I, ctypes.POINTER(_D), _VP]),
+    "glm_sur_batch_setup": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_I), _VP, _VP, ctypes.POINTER(GlmSurOpts), _VP]),
+    "glm_sur_batch_get_setup_status": (_I, [_VP]),
+    "glm_sur_batch_solve": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
+    "glm_sur_batch_get_status": (_I, [_VP, ctypes.POINTER(_I)]),
+    "glm_sur_batch_tile": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "glm_sur_batch_launch_count": (ctypes.c_int64, [_VP]),
+    "glm_sur_batch_destroy": (None, [_VP]),
     "glm_sur_status_string": (ctypes.c_char_p, [_I]),
     "glm_sur_version": (ctypes.c_char_p, []),
 }
@@ -168,6 +176,48 @@ def glm_sur_ols_static(h: int, Y_ptr: int, ldy: int, k: int, b_ptr: int, ldb: in
 
 def glm_sur_destroy(h: int) -> None:
     lib().glm_sur_destroy(h)
+
+
+def glm_sur_batch_setup(count: int, G, M, n_i, X_ptr: int, Omega_ptr: int, opts, stream: int) -> int:
+    h = ctypes.c_void_p()
+    ga = (ctypes.c_int * count)(*[int(v) for v in G])
+    ma = (ctypes.c_int * count)(*[int(v) for v in M])
+    na = (ctypes.c_int * len(n_i))(*[int(v) for v in n_i])
+    rc = lib().glm_sur_batch_setup(ctypes.byref(h), count, ga, ma, na, X_ptr, Omega_ptr,
+                                   ctypes.byref(opts) if opts is not None else None, stream)
+    check(rc, "glm_sur_batch_setup")
+    return h.value
+
+
+def glm_sur_batch_get_setup_status(h: int) -> int:
+    return int(lib().glm_sur_batch_get_setup_status(h))
+
+
+def glm_sur_batch_solve(h: int, Y_ptr: int, k: int, b_ptr: int, iters_ptr: int, relres_ptr: int,
+                        stream: int) -> None:
+    check(lib().glm_sur_batch_solve(h, Y_ptr, k, b_ptr, iters_ptr, relres_ptr, stream), "glm_sur_batch_solve")
+
+
+def glm_sur_batch_get_status(h: int, n: int):
+    arr = (ctypes.c_int * n)()
+    rc = lib().glm_sur_batch_get_status(h, arr)
+    if rc in (GLM_SUR_INVALID_ARG, GLM_SUR_CUDA_ERROR):
+        check(rc, "glm_sur_batch_get_status")
+    return [int(v) for v in arr]
+
+
+def glm_sur_batch_tile(h: int):
+    ms = (ctypes.c_float * 3)()
+    t = int(lib().glm_sur_batch_tile(h, ms))
+    return t, [float(v) for v in ms]
+
+
+def glm_sur_batch_launch_count(h: int) -> int:
+    return int(lib().glm_sur_batch_launch_count(h))
+
+
+def glm_sur_batch_destroy(h: int) -> None:
+    lib().glm_sur_batch_destroy(h)
 
 
 def glm_sur_version() -> str:

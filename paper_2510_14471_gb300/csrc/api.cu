@@ -618,8 +618,11 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   SETUP_TRY(cudaMemsetAsync(h->setup_flags, 0, sizeof(int), s));
   // TSQR of every block
   QrPlan plan;
-  build_qr_plan(G, M, h->n_i, plan);
-  rc = run_qr(plan, X, ldx, gm.d_off, gm.d_poff, gm.d_r_off, h->Q64, gm.np, h->R, h->setup_flags, s);
+  std::vector<QrBlock> qb(G);
+  for (int i = 0; i < G; ++i)
+    qb[i] = QrBlock{n_i[i], M, (int64_t)h->off[i] * ldx, ldx, (int64_t)h->poff[i], (int64_t)gm.np};
+  build_qr_plan(qb, plan);
+  rc = run_qr(plan, X, gm.d_r_off, h->Q64, h->R, h->setup_flags, s);
   if (rc != GLM_SUR_OK) return bail(rc);
   if (o.precision == GLM_SUR_PREC_FP32_REFINE) {
     SETUP_TRY(dalloc(&h->Q32, (size_t)M * gm.np));
@@ -739,7 +742,9 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
   } else {
     // float64 iterative refinement on P Sigma w = P y (w in null(X^T)) with
     // float32 inner PCG.  A correction that increases a column's float64
-    // residual is taken back and the column stops (its best w is kept).
+    // residual is taken back and the column stops (its best w is kept); one
+    // that does not at least halve it is kept and the column stops too: the
+    // residual has reached its float64 rounding floor.
     GS_CUDA_TRY(cudaMemsetAsync(h->w64, 0, mk * sizeof(double), s));
     GS_CUDA_TRY(cudaMemsetAsync(h->d_iters_acc, 0, k * sizeof(int), s));
     std::vector<double> rho0(k, 0.0), prev(k, 0.0), cur(k, 0.0), rr_out(k, 0.0);
@@ -766,8 +771,10 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
             fin[j] = (rr_out[j] <= h->opts.tol) ? GLM_SUR_OK : GLM_SUR_STAGNATED;
           } else {
             rr_out[j] = rr;
+            const bool floor = outer > 0 && cur[j] > kRefineMinGain * prev[j];
             prev[j] = cur[j];
             if (rr <= h->opts.tol) fin[j] = GLM_SUR_OK;
+            else if (floor) fin[j] = GLM_SUR_STAGNATED;
             else if (outer >= h->opts.max_refine) fin[j] = GLM_SUR_NOT_CONVERGED;
           }
         }

@@ -1,0 +1,347 @@
+// C ABI of the batched solver: setup of many SUR instances (TSQR of all their
+// blocks in shared level launches), and one-launch solves with a small
+// autotuner for the tile height.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "batch.h"
+#include "common.cuh"
+#include "glm_sur.h"
+#include "internal.h"
+#include "pcg.h"
+
+using namespace glmsur;
+
+struct glm_sur_batch_ctx {
+  int count = 0, sms = 148, maxG = 0, maxNp = 0, maxNq = 0;
+  glm_sur_opts opts;
+  std::vector<int> G, M, n, np, nq, blk0, quad0;
+  std::vector<int64_t> q_off, om_off, x_off, m_sum;   // per instance
+  int nblk = 0, nquad = 0;
+  int64_t q_elems = 0, om_elems = 0, r_elems = 0, v_rows = 0;  // v_rows = sum M*G
+  double *q64 = nullptr, *R = nullptr, *om64 = nullptr;
+  float *q32 = nullptr, *om32 = nullptr;
+  int *d_n_i = nullptr, *d_poff = nullptr, *d_quad_blk = nullptr, *setup_flags = nullptr;
+  int64_t* d_r_off = nullptr;
+  // solve workspace
+  int kcap = 0;
+  double *w64 = nullptr, *E64 = nullptr, *d64 = nullptr;
+  float *g32 = nullptr, *u32 = nullptr, *w32 = nullptr, *wb32 = nullptr;
+  int *status = nullptr, *iters_d = nullptr, *counter = nullptr;
+  double* relres_d = nullptr;
+  BatchInst* d_insts = nullptr;
+  int insts_k = 0;
+  int last_k = 0;
+  int tile = 0;          // autotuned tile height (0 = not tuned yet)
+  float tune_ms[3] = {0, 0, 0};
+  int grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int graph_k = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t balloc(T** p, size_t n) {
+  *p = nullptr;
+  return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+template <typename T>
+void bfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_solve(glm_sur_batch_ctx* h) {
+  bfree(h->w64); bfree(h->E64); bfree(h->d64); bfree(h->g32); bfree(h->u32); bfree(h->w32); bfree(h->wb32);
+  bfree(h->status); bfree(h->iters_d); bfree(h->relres_d); bfree(h->d_insts);
+  h->kcap = 0;
+  h->insts_k = 0;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+// Omega of every instance into the padded G x Gq pools (float64 and float32).
+__global__ void k_pad_omegas(int count, const int* __restrict__ G, const int64_t* __restrict__ src_off,
+                             const int64_t* __restrict__ dst_off, const double* __restrict__ Om, double* om64,
+                             float* om32) {
+  const int j = blockIdx.x;
+  if (j >= count) return;
+  const int g = G[j], gq = (g + 3) & ~3;
+  for (int e = threadIdx.x; e < g * gq; e += blockDim.x) {
+    const int r = e / gq, c = e % gq;
+    const double v = c < g ? Om[src_off[j] + (int64_t)c * g + r] : 0.0;
+    om64[dst_off[j] + e] = v;
+    om32[dst_off[j] + e] = (float)v;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G, const int* M, const int* n_i,
+                                   const double* X, const double* Omega, const glm_sur_opts* opts,
+                                   glm_sur_stream_t stream) {
+  if (!out || count < 1 || !G || !M || !n_i || !X || !Omega) return GLM_SUR_INVALID_ARG;
+  *out = nullptr;
+  glm_sur_opts o;
+  glm_sur_default_opts(&o);
+  if (opts) o = *opts;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  glm_sur_batch_ctx* h = new glm_sur_batch_ctx();
+  h->count = count;
+  h->opts = o;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<int> blk_n, blk_poff, quad_blk;
+  std::vector<int64_t> blk_roff;
+  std::vector<QrBlock> qb;
+  int64_t xo = 0, mo = 0;
+  for (int j = 0; j < count; ++j) {
+    const int g = G[j], mm = M[j];
+    if (g < 1 || g > kBatchMaxG || mm < 1) { delete h; return GLM_SUR_INVALID_ARG; }
+    int n = 0, np = 0;
+    h->blk0.push_back(h->nblk);
+    h->quad0.push_back(h->nquad);
+    h->q_off.push_back(h->q_elems);
+    h->om_off.push_back(h->om_elems);
+    h->x_off.push_back(xo);
+    h->m_sum.push_back(mo);
+    for (int i = 0; i < g; ++i) {
+      const int ni = n_i[h->nblk + i];
+      if (ni < 1 || ni > kBatchMaxCols || ni > mm) { delete h; return GLM_SUR_INVALID_ARG; }
+      blk_n.push_back(ni);
+      blk_poff.push_back(np);
+      blk_roff.push_back(h->r_elems);
+      qb.push_back(QrBlock{ni, mm, xo + (int64_t)n * mm, mm, h->q_elems + np, 0});
+      for (int q = 0; q < round_up4(ni) / 4; ++q) quad_blk.push_back(i);
+      n += ni;
+      np += round_up4(ni);
+      h->r_elems += (int64_t)ni * ni;
+    }
+    if (np > kBatchMaxNp || (np / 4) * kBatchMaxK > 4 * 256) { delete h; return GLM_SUR_INVALID_ARG; }
+    for (int i = 0; i < g; ++i) qb[h->nblk + i].q_ld = np;
+    h->G.push_back(g); h->M.push_back(mm); h->n.push_back(n); h->np.push_back(np); h->nq.push_back(np / 4);
+    h->nblk += g;
+    h->nquad += np / 4;
+    h->q_elems += (int64_t)mm * np;
+    h->om_elems += (int64_t)g * round_up4(g);
+    h->v_rows += (int64_t)mm * g;
+    h->maxG = std::max(h->maxG, g);
+    h->maxNp = std::max(h->maxNp, np);
+    h->maxNq = std::max(h->maxNq, np / 4);
+    xo += (int64_t)mm * n;
+    mo += (int64_t)g * g;
+  }
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_last_error(e, what, __FILE__, __LINE__);
+    glm_sur_batch_destroy(h);
+    return e == cudaErrorMemoryAllocation ? GLM_SUR_OOM : GLM_SUR_CUDA_ERROR;
+  };
+  cudaError_t e;
+#define BTRY(x) if ((e = (x)) != cudaSuccess) return fail(e, #x)
+  BTRY(balloc(&h->q64, h->q_elems));
+  BTRY(balloc(&h->q32, h->q_elems));
+  BTRY(balloc(&h->R, h->r_elems));
+  BTRY(balloc(&h->om64, h->om_elems));
+  BTRY(balloc(&h->om32, h->om_elems));
+  BTRY(balloc(&h->d_n_i, h->nblk));
+  BTRY(balloc(&h->d_poff, h->nblk));
+  BTRY(balloc(&h->d_r_off, h->nblk));
+  BTRY(balloc(&h->d_quad_blk, h->nquad));
+  BTRY(balloc(&h->setup_flags, 1));
+  BTRY(balloc(&h->counter, 1));
+  BTRY(cudaMemcpy(h->d_n_i, blk_n.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(h->d_poff, blk_poff.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(h->d_r_off, blk_roff.data(), sizeof(int64_t) * h->nblk, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(h->d_quad_blk, quad_blk.data(), sizeof(int) * h->nquad, cudaMemcpyHostToDevice));
+  BTRY(cudaMemsetAsync(h->q64, 0, sizeof(double) * h->q_elems, s));
+  BTRY(cudaMemsetAsync(h->setup_flags, 0, sizeof(int), s));
+  // Omega pools
+  {
+    int* dG = nullptr;
+    int64_t *dsrc = nullptr, *ddst = nullptr;
+    BTRY(balloc(&dG, count));
+    BTRY(balloc(&dsrc, count));
+    BTRY(balloc(&ddst, count));
+    BTRY(cudaMemcpy(dG, h->G.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+    BTRY(cudaMemcpy(dsrc, h->m_sum.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
+    BTRY(cudaMemcpy(ddst, h->om_off.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
+    k_pad_omegas<<<count, 128, 0, s>>>(count, dG, dsrc, ddst, Omega, h->om64, h->om32);
+    BTRY(cudaGetLastError());
+    BTRY(cudaStreamSynchronize(s));
+    cudaFree(dG); cudaFree(dsrc); cudaFree(ddst);
+  }
+  // TSQR of every block of every instance
+  QrPlan plan;
+  build_qr_plan(qb, plan);
+  glm_sur_status rc = run_qr(plan, X, h->d_r_off, h->q64, h->R, h->setup_flags, s);
+  if (rc != GLM_SUR_OK) { glm_sur_batch_destroy(h); return rc; }
+  launch_convert<double, float>(h->q_elems, h->q64, h->q32, 1.0, s);
+  BTRY(cudaGetLastError());
+  h->launches += 2 * (int64_t)plan.level_first.size() + 2;
+#undef BTRY
+  *out = h;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_batch_get_setup_status(glm_sur_batch_t h) {
+  if (!h) return GLM_SUR_INVALID_ARG;
+  int flags = 0;
+  GS_CUDA_TRY(cudaMemcpy(&flags, h->setup_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flags & 2) return GLM_SUR_NONFINITE;
+  if (flags & 1) return GLM_SUR_RANK_DEFICIENT;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, double* b, int* iters,
+                                   double* relres, glm_sur_stream_t stream) {
+  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  if (k != 1 && k != 2 && k != 4 && k != 8) return GLM_SUR_INVALID_ARG;
+  if (h->maxNq * k > 4 * 256) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (k > h->kcap) {
+    free_solve(h);
+    const size_t nv = (size_t)h->v_rows * k;
+    GS_CUDA_TRY(balloc(&h->w64, nv)); GS_CUDA_TRY(balloc(&h->E64, nv)); GS_CUDA_TRY(balloc(&h->d64, nv));
+    GS_CUDA_TRY(balloc(&h->g32, nv)); GS_CUDA_TRY(balloc(&h->u32, nv)); GS_CUDA_TRY(balloc(&h->w32, nv));
+    GS_CUDA_TRY(balloc(&h->wb32, nv));
+    GS_CUDA_TRY(balloc(&h->status, (size_t)h->count * k));
+    GS_CUDA_TRY(balloc(&h->iters_d, (size_t)h->count * k));
+    GS_CUDA_TRY(balloc(&h->relres_d, (size_t)h->count * k));
+    GS_CUDA_TRY(balloc(&h->d_insts, (size_t)h->count));
+    h->kcap = k;
+  }
+  if (h->insts_k != k) {
+    // work order: most expensive instances first (cost ~ M * (G^2 + 2 n')), so
+    // the persistent CTAs finish together
+    std::vector<int> order(h->count);
+    for (int j = 0; j < h->count; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      const double ca = (double)h->M[a] * (h->G[a] * h->G[a] + 2.0 * h->np[a]);
+      const double cc = (double)h->M[c] * (h->G[c] * h->G[c] + 2.0 * h->np[c]);
+      return ca > cc;
+    });
+    std::vector<int64_t> voff(h->count), yoff(h->count), boff(h->count);
+    int64_t v = 0, y = 0, bo = 0;
+    for (int j = 0; j < h->count; ++j) {
+      voff[j] = v; yoff[j] = y; boff[j] = bo;
+      v += (int64_t)h->M[j] * h->G[j] * k;
+      y += (int64_t)h->M[j] * h->G[j] * k;
+      bo += (int64_t)h->n[j] * k;
+    }
+    std::vector<BatchInst> insts(h->count);
+    for (int r = 0; r < h->count; ++r) {
+      const int j = order[r];
+      BatchInst& d = insts[r];
+      d.index = j;
+      d.G = h->G[j]; d.Gq = round_up4(h->G[j]); d.M = h->M[j]; d.n = h->n[j]; d.np = h->np[j]; d.nq = h->nq[j];
+      d.blk0 = h->blk0[j]; d.quad0 = h->quad0[j];
+      d.q_off = h->q_off[j]; d.om_off = h->om_off[j]; d.v_off = voff[j]; d.y_off = yoff[j]; d.b_off = boff[j];
+    }
+    GS_CUDA_TRY(cudaMemcpy(h->d_insts, insts.data(), sizeof(BatchInst) * h->count, cudaMemcpyHostToDevice));
+    h->insts_k = k;
+    h->tile = 0;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  BatchPools P{h->q64, h->q32, h->R, h->om64, h->om32, h->d_n_i, h->d_poff, h->d_r_off, h->d_quad_blk,
+               h->w64, h->E64, h->d64, h->g32, h->u32, h->w32, h->wb32, Y, b, h->status, h->iters_d,
+               h->relres_d};
+  BatchOpts bo{h->opts.tol, h->opts.inner_tol, h->opts.max_refine, 4000, 25};
+  if (h->tile == 0) {
+    // autotune: time one batch solve per tile height, keep the fastest
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int t = 0; t < 3; ++t) {
+      const int TR = kBatchTiles[t];
+      int ctas = 0;
+      GS_CUDA_TRY(batch_prepare(k, TR, h->maxG, h->maxNp, &ctas));
+      if (ctas < 1) { h->tune_ms[t] = -1; continue; }
+      const int grid = h->sms * ctas;
+      cudaEventRecord(e0, s);
+      GS_CUDA_TRY(batch_solve_launch(k, TR, h->d_insts, h->count, P, bo, h->counter, grid, h->maxG, h->maxNp, s));
+      cudaEventRecord(e1, s);
+      GS_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      h->tune_ms[t] = ms;
+      h->launches += 2;
+      if (ms < best) { best = ms; h->tile = TR; h->grid = grid; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (h->tile == 0) return GLM_SUR_INVALID_ARG;
+  }
+  // one persistent launch, replayed from a captured graph while the buffers stay the same
+  const void* key[5] = {Y, b, iters, relres, nullptr};
+  if (!h->graph || h->graph_k != k || std::memcmp(key, h->graph_key, sizeof key) != 0) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    cudaStream_t cs;
+    GS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    GS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    batch_solve_launch(k, h->tile, h->d_insts, h->count, P, bo, h->counter, h->grid, h->maxG, h->maxNp, cs);
+    if (iters) cudaMemcpyAsync(iters, h->iters_d, sizeof(int) * h->count * k, cudaMemcpyDeviceToDevice, cs);
+    if (relres) cudaMemcpyAsync(relres, h->relres_d, sizeof(double) * h->count * k, cudaMemcpyDeviceToDevice, cs);
+    GS_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      set_last_error(e, "cudaGraphInstantiate(batch)", __FILE__, __LINE__);
+      h->graph = nullptr;
+      return GLM_SUR_CUDA_ERROR;
+    }
+    std::memcpy(h->graph_key, key, sizeof key);
+    h->graph_k = k;
+  }
+  GS_CUDA_TRY(cudaGraphLaunch(h->graph, s));
+  h->launches += 2;
+  h->last_k = k;
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status) {
+  if (!h || !status || h->last_k < 1) return GLM_SUR_INVALID_ARG;
+  GS_CUDA_TRY(cudaDeviceSynchronize());
+  GS_CUDA_TRY(cudaMemcpy(status, h->status, sizeof(int) * h->count * h->last_k, cudaMemcpyDeviceToHost));
+  glm_sur_status worst = GLM_SUR_OK;
+  for (int j = 0; j < h->count * h->last_k; ++j) {
+    if (status[j] == kStatusRunning) status[j] = GLM_SUR_NOT_CONVERGED;
+    if (status[j] != GLM_SUR_OK && status[j] != GLM_SUR_STAGNATED && worst == GLM_SUR_OK)
+      worst = (glm_sur_status)status[j];
+  }
+  return worst;
+}
+
+int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms) {
+  if (!h) return -1;
+  if (tune_ms)
+    for (int t = 0; t < 3; ++t) tune_ms[t] = h->tune_ms[t];
+  return h->tile;
+}
+
+int64_t glm_sur_batch_launch_count(glm_sur_batch_t h) { return h ? h->launches : -1; }
+
+void glm_sur_batch_destroy(glm_sur_batch_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_solve(h);
+  bfree(h->q64); bfree(h->q32); bfree(h->R); bfree(h->om64); bfree(h->om32);
+  bfree(h->d_n_i); bfree(h->d_poff); bfree(h->d_r_off); bfree(h->d_quad_blk); bfree(h->setup_flags);
+  bfree(h->counter);
+  delete h;
+}
+
+}  // extern "C"

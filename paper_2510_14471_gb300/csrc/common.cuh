@@ -26,6 +26,9 @@ void set_last_error(cudaError_t e, const char* what, const char* file, int line)
 // Per-column run status codes kept on the device while a PCG runs.  Column
 // states use the public glm_sur_status values; RUNNING marks a live column.
 constexpr int kStatusRunning = -1;
+// An iterative-refinement step whose float64 residual is above this fraction
+// of the previous one has met the rounding floor of the residual itself.
+constexpr double kRefineMinGain = 0.5;
 
 // ---------------------------------------------------------------------------
 // small device helpers

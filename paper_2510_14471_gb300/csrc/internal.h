@@ -28,6 +28,16 @@ struct QrNode {
   int64_t out_off;     // where this node's R goes inside the parent's stack
   int64_t v_off;       // reflectors (rows x nc, col-major)
   int64_t tau_off;
+  int64_t x_base;      // leaf input: element offset of the block's first column in X
+  int64_t x_ld;        //   and its leading dimension (column-major)
+  int64_t q_base;      // explicit Q: element offset of the block's (row 0, column 0) in Q
+  int64_t q_ld;        //   and its row stride (row-major)
+};
+
+// One regressor block to factor: rows x nc, read from X and written to Q.
+struct QrBlock {
+  int nc;
+  int64_t rows, x_base, x_ld, q_base, q_ld;
 };
 
 struct QrPlan {
@@ -37,9 +47,8 @@ struct QrPlan {
   size_t max_smem_factor = 0, max_smem_form = 0;
 };
 
-void build_qr_plan(int G, int64_t M, const std::vector<int>& n_i, QrPlan& plan);
-glm_sur_status run_qr(const QrPlan& plan, const double* X, int64_t ldx, const int* d_col_off,
-                      const int* d_pcol_off, const int64_t* d_r_off, double* Q, int64_t ldq, double* R,
+void build_qr_plan(const std::vector<QrBlock>& blocks, QrPlan& plan);
+glm_sur_status run_qr(const QrPlan& plan, const double* X, const int64_t* d_r_off, double* Q, double* R,
                       int* d_setup_flags, cudaStream_t st);
 
 // Geometry of one SUR problem on the device.

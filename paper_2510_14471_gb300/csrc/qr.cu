@@ -73,8 +73,8 @@ __device__ void householder_qr_smem(double* A, int rows, int nc, double* tau, do
 
 __global__ void __launch_bounds__(kQrThreads)
 qr_factor_level(const QrNode* __restrict__ nodes, int first, int count, const double* __restrict__ X,
-                int64_t ldx, const int* __restrict__ col_off, double* stack, double* V, double* tau_ws,
-                double* Rout, const int64_t* __restrict__ r_off, int* setup_flags) {
+                double* stack, double* V, double* tau_ws, double* Rout, const int64_t* __restrict__ r_off,
+                int* setup_flags) {
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double tau_s[kMaxBlockCols];
@@ -85,10 +85,10 @@ qr_factor_level(const QrNode* __restrict__ nodes, int first, int count, const do
   double* A = sm;
   // load the node's input
   if (nd.level == 0) {
-    const double* src = X + (int64_t)col_off[nd.blk] * ldx + nd.in_off;
+    const double* src = X + nd.x_base + nd.in_off;
     for (int64_t e = threadIdx.x; e < (int64_t)rows * nc; e += blockDim.x) {
       const int c = (int)(e / rows), r = (int)(e % rows);
-      A[e] = src[(int64_t)c * ldx + r];
+      A[e] = src[(int64_t)c * nd.x_ld + r];
     }
   } else {
     const double* src = stack + nd.in_off;
@@ -136,8 +136,7 @@ qr_factor_level(const QrNode* __restrict__ nodes, int first, int count, const do
 // Explicit Q of one node: B = H_0 ... H_{nc-1} [E; 0].
 __global__ void __launch_bounds__(kQrThreads)
 qr_form_q_level(const QrNode* __restrict__ nodes, int first, int count, double* stack,
-                const double* __restrict__ V, const double* __restrict__ tau_ws, double* Q, int64_t ldq,
-                const int* __restrict__ pcol_off) {
+                const double* __restrict__ V, const double* __restrict__ tau_ws, double* Q) {
   extern __shared__ double sm[];
   const int id = blockIdx.x;
   if (id >= count) return;
@@ -177,10 +176,10 @@ qr_form_q_level(const QrNode* __restrict__ nodes, int first, int count, double* 
   }
   if (nd.level == 0) {
     // leaf: rows of Q_i into the padded row-major Q
-    double* dst = Q + nd.in_off * ldq + pcol_off[nd.blk];
+    double* dst = Q + nd.q_base + nd.in_off * nd.q_ld;
     for (int64_t e = threadIdx.x; e < (int64_t)rows * nc; e += blockDim.x) {
       const int r = (int)(e / nc), c = (int)(e % nc);
-      dst[(int64_t)r * ldq + c] = B[(int64_t)c * rows + r];
+      dst[(int64_t)r * nd.q_ld + c] = B[(int64_t)c * rows + r];
     }
   } else {
     double* dst = stack + nd.in_off;
@@ -190,15 +189,18 @@ qr_form_q_level(const QrNode* __restrict__ nodes, int first, int count, double* 
 
 }  // namespace
 
-// Build the TSQR forest for blocks with widths n_i and M rows (host).
-void build_qr_plan(int G, int64_t M, const std::vector<int>& n_i, QrPlan& plan) {
+// Build the TSQR forest of a list of blocks (host).  Block b is R factor b
+// (r_off[b]) of the caller.
+void build_qr_plan(const std::vector<QrBlock>& blocks, QrPlan& plan) {
   plan.nodes.clear();
   plan.level_first.clear();
   plan.level_count.clear();
   std::vector<std::vector<QrNode>> by_level;
   int64_t stack_sz = 0, v_sz = 0, tau_sz = 0;
+  const int G = (int)blocks.size();
   for (int b = 0; b < G; ++b) {
-    const int nc = n_i[b];
+    const int nc = blocks[b].nc;
+    const int64_t M = blocks[b].rows;
     const int TL = (nc <= 32) ? 256 : 128;
     // level 0: even row chunks
     const int64_t nch = std::max<int64_t>(1, ceil_div(M, TL));
@@ -206,6 +208,8 @@ void build_qr_plan(int G, int64_t M, const std::vector<int>& n_i, QrPlan& plan) 
     for (int64_t c = 0; c < nch; ++c) {
       QrNode nd{};
       nd.blk = b; nd.nc = nc; nd.level = 0;
+      nd.x_base = blocks[b].x_base; nd.x_ld = blocks[b].x_ld;
+      nd.q_base = blocks[b].q_base; nd.q_ld = blocks[b].q_ld;
       const int64_t s = (M * c) / nch, e = (M * (c + 1)) / nch;
       nd.rows = (int)(e - s);
       nd.in_off = s;
@@ -269,8 +273,7 @@ void build_qr_plan(int G, int64_t M, const std::vector<int>& n_i, QrPlan& plan) 
   }
 }
 
-glm_sur_status run_qr(const QrPlan& plan, const double* X, int64_t ldx, const int* d_col_off,
-                      const int* d_pcol_off, const int64_t* d_r_off, double* Q, int64_t ldq, double* R,
+glm_sur_status run_qr(const QrPlan& plan, const double* X, const int64_t* d_r_off, double* Q, double* R,
                       int* d_setup_flags, cudaStream_t st) {
   QrNode* d_nodes = nullptr;
   double *stack = nullptr, *V = nullptr, *tau = nullptr;
@@ -295,13 +298,12 @@ glm_sur_status run_qr(const QrPlan& plan, const double* X, int64_t ldx, const in
   const int L = (int)plan.level_first.size();
   for (int l = 0; rc == GLM_SUR_OK && l < L; ++l) {
     qr_factor_level<<<plan.level_count[l], kQrThreads, plan.max_smem_factor, st>>>(
-        d_nodes, plan.level_first[l], plan.level_count[l], X, ldx, d_col_off, stack, V, tau, R, d_r_off,
-        d_setup_flags);
+        d_nodes, plan.level_first[l], plan.level_count[l], X, stack, V, tau, R, d_r_off, d_setup_flags);
     if ((e = cudaGetLastError()) != cudaSuccess) fail(e, "qr_factor_level");
   }
   for (int l = L - 1; rc == GLM_SUR_OK && l >= 0; --l) {
     qr_form_q_level<<<plan.level_count[l], kQrThreads, plan.max_smem_form, st>>>(
-        d_nodes, plan.level_first[l], plan.level_count[l], stack, V, tau, Q, ldq, d_pcol_off);
+        d_nodes, plan.level_first[l], plan.level_count[l], stack, V, tau, Q);
     if ((e = cudaGetLastError()) != cudaSuccess) fail(e, "qr_form_q_level");
   }
   if (tau) cudaFreeAsync(tau, st);

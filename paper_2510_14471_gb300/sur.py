@@ -133,3 +133,68 @@ class GlmSur:
             self.close()
         except Exception:
             pass
+
+
+class GlmSurBatch:
+    """Many independent SUR instances solved in one persistent launch.
+
+    problems: list of (X_blocks, Omega) pairs (numpy or torch, float64).
+    tol defaults to 1e-12: the float64 residual of a refined batched solve
+    settles at a few 1e-13, below which refinement steps buy nothing."""
+
+    def __init__(self, problems, tol: float = 1e-12, inner_tol: float = 1e-5, max_refine: int = 8,
+                 device="cuda"):
+        self.device = torch.device(device)
+        self.G = [len(xb) for xb, _ in problems]
+        self.M = [int(xb[0].shape[0]) for xb, _ in problems]
+        self.n_i = [int(x.shape[1]) for xb, _ in problems for x in xb]
+        self.n = [sum(int(x.shape[1]) for x in xb) for xb, _ in problems]
+        self.m = [g * mm for g, mm in zip(self.G, self.M)]
+        xs = []
+        for xb, _ in problems:
+            xs.append(torch.cat([_dev_f64(x, self.device).t() for x in xb], dim=0).reshape(-1))
+        self._X = torch.cat(xs).contiguous()
+        self._Om = torch.cat([_dev_f64(om, self.device).t().reshape(-1) for _, om in problems]).contiguous()
+        self.opts = L.default_opts()
+        self.opts.tol = tol
+        self.opts.inner_tol = inner_tol
+        self.opts.max_refine = max_refine
+        self._h = L.glm_sur_batch_setup(len(problems), self.G, self.M, self.n_i, self._X.data_ptr(),
+                                        self._Om.data_ptr(), self.opts, torch.cuda.current_stream().cuda_stream)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def setup_status(self) -> int:
+        return L.glm_sur_batch_get_setup_status(self._h)
+
+    def pack_y(self, Ys):
+        """List of (m_j, k) arrays -> one device buffer in the ABI layout."""
+        return torch.cat([_dev_f64(y, self.device).t().reshape(-1) for y in Ys]).contiguous()
+
+    def solve(self, Ys, k: int):
+        Y = self.pack_y(Ys) if isinstance(Ys, (list, tuple)) else Ys
+        b = torch.empty(sum(self.n) * k, dtype=torch.float64, device=self.device)
+        cnt = len(self.G)
+        iters = torch.zeros(cnt * k, dtype=torch.int32, device=self.device)
+        relres = torch.zeros(cnt * k, dtype=torch.float64, device=self.device)
+        L.glm_sur_batch_solve(self._h, Y.data_ptr(), k, b.data_ptr(), iters.data_ptr(), relres.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+        status = L.glm_sur_batch_get_status(self._h, cnt * k)
+        out, off = [], 0
+        for nj in self.n:
+            out.append(b[off:off + nj * k].view(k, nj).t())
+            off += nj * k
+        return out, iters.view(cnt, k), relres.view(cnt, k), status
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            L.glm_sur_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
