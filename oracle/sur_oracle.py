@@ -23,6 +23,8 @@ of General Linear Models"):
   * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
                              Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
   * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
+  * ``sur_gls_gradient_kron`` -- the same adjoint for positive definite Omega
+    through Sigma^-1 = Omega^-1 (x) I_M (medium sizes, no m x m matrix).
 
 Layouts: X_blocks list of (M, n_i); Omega (G, G); Y (m, k) with column j =
 vec(Y_j) (block i occupies rows i*M .. (i+1)*M); b (n, k).
@@ -37,7 +39,7 @@ import numpy as np
 __all__ = [
     "sur_dense", "augmented_matrix", "aug_dense_solve", "gls_formula", "aug_lemma",
     "ols_blocks", "sur_gls_structured", "pcg", "sur_pcg_aug", "rglm_pcg_aug",
-    "sur_gls_gradient", "augmented_residual", "lse_solve",
+    "sur_gls_gradient", "sur_gls_gradient_kron", "augmented_residual", "lse_solve",
 ]
 
 
@@ -562,3 +564,48 @@ def sur_gls_gradient(X_blocks, Omega, Y, dL_db):
         Wm = w[:, c].reshape(G, M).T
         gO -= Lm.T @ Wm
     return lam, gO
+
+
+def sur_gls_gradient_kron(X_blocks, Omega, Y, dL_db):
+    """Adjoint of eq. (aug1) for positive definite Omega, without forming any
+    m x m matrix (eq. (GLS) with Sigma^-1 = Omega^-1 (x) I_M):
+
+      A   = X^T Sigma^-1 X,  block (i, j) = (Omega^-1)_ij X_i^T X_j
+      b   = A^-1 X^T Sigma^-1 y,        w  = Sigma^-1 (y - X b)
+      lam = Sigma^-1 X A^-1 (dL/db),    mu = -A^-1 (dL/db)
+
+    (w; b) and (lam; mu) solve eq. (aug1) with right-hand sides (y; 0) and
+    (0; dL/db):  Sigma lam + X mu = 0 and X^T lam = dL/db.  With M x G
+    matrices W, Lam (vec(W) = w, vec(Lam) = lam), Sigma^-1 v = vec(V Omega^-1)
+    and dL/dOmega = -sum over right-hand sides of Lam^T W (unsymmetrised).
+    Returns (b (n, k), w (m, k), lam (m, k), dL_dOmega (G, G))."""
+    G = len(X_blocks)
+    M = X_blocks[0].shape[0]
+    n_i = [x.shape[1] for x in X_blocks]
+    n = sum(n_i)
+    offs = np.cumsum([0] + n_i)
+    blk = np.repeat(np.arange(G), n_i)
+    Oi = np.linalg.inv(Omega)
+    Xc = np.hstack(X_blocks)                                   # M x n
+    A = Oi[np.ix_(blk, blk)] * (Xc.T @ Xc)
+    Y = np.asarray(Y, dtype=float).reshape(G * M, -1)
+    gb = np.asarray(dL_db, dtype=float).reshape(n, -1)
+    k = Y.shape[1]
+    b = np.empty((n, k)); w = np.empty((G * M, k)); lam = np.empty((G * M, k))
+    gO = np.zeros((G, G))
+
+    def xt(V):        # X^T vec(V), V: M x G
+        return np.concatenate([X_blocks[i].T @ V[:, i] for i in range(G)])
+
+    def x_of(c):      # X c as an M x G matrix
+        return np.column_stack([X_blocks[i] @ c[offs[i]:offs[i + 1]] for i in range(G)])
+
+    for c in range(k):
+        Ym = Y[:, c].reshape(G, M).T
+        b[:, c] = np.linalg.solve(A, xt(Ym @ Oi))
+        Wm = (Ym - x_of(b[:, c])) @ Oi
+        Lm = x_of(np.linalg.solve(A, gb[:, c])) @ Oi
+        w[:, c] = Wm.T.reshape(-1)
+        lam[:, c] = Lm.T.reshape(-1)
+        gO -= Lm.T @ Wm
+    return b, w, lam, gO

@@ -278,6 +278,41 @@ def test_gradient_matches_finite_differences():
         assert abs(fd - np.sum(gO * E)) < 1e-6 * max(1.0, abs(fd))
 
 
+def test_kron_gradient_matches_dense_adjoint():
+    # the Kronecker-inverse adjoint against the dense augmented-system adjoint
+    for seed, omega in ((42, "chol"), (43, "wishart"), (44, "spectrum")):
+        p = S.make_problem(G=4, M=9, n_i=[2, 3, 1, 2], k=2, seed=seed, omega=omega)
+        gb = S.rng(seed + 100).standard_normal((p.n, 2))
+        w_d, b_d = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
+        lam_d, gO_d = O.sur_gls_gradient(p.X_blocks, p.Omega, p.Y, gb)
+        b, w, lam, gO = O.sur_gls_gradient_kron(p.X_blocks, p.Omega, p.Y, gb)
+        assert rel(b, b_d) < 1e-10 and rel(w, w_d) < 1e-9
+        assert rel(lam, lam_d) < 1e-9 and rel(gO, gO_d) < 1e-9
+
+
+def test_kron_gradient_finite_differences_medium():
+    # directional central differences of L(b) = ||b - target||^2 at G = 8, M = 60
+    p = S.make_problem(G=8, M=60, n_i=[3, 5, 2, 4, 6, 3, 2, 5], k=1, seed=45, omega="chol")
+    target = S.rng(46).standard_normal((p.n, 1))
+
+    def loss(Y, Om):
+        return float(np.sum((O.gls_formula(p.X_blocks, Om, Y) - target) ** 2))
+
+    b, w, lam, gO = O.sur_gls_gradient_kron(p.X_blocks, p.Omega, p.Y, 0 * target)
+    b, w, lam, gO = O.sur_gls_gradient_kron(p.X_blocks, p.Omega, p.Y, 2 * (b - target))
+    # adjoint identity X^T lam = dL/db
+    xtl = np.concatenate([p.X_blocks[i].T @ lam[i * p.M:(i + 1) * p.M, 0] for i in range(p.G)])
+    assert rel(xtl, 2 * (b - target)[:, 0]) < 1e-10
+    h, g = 1e-6, S.rng(47)
+    for _ in range(3):
+        dY = g.standard_normal(p.Y.shape)
+        fd = (loss(p.Y + h * dY, p.Omega) - loss(p.Y - h * dY, p.Omega)) / (2 * h)
+        assert abs(fd - np.sum(lam * dY)) < 1e-6 * max(1.0, abs(fd))
+        E = g.standard_normal((p.G, p.G)); E = E + E.T
+        fd = (loss(p.Y, p.Omega + h * E) - loss(p.Y, p.Omega - h * E)) / (2 * h)
+        assert abs(fd - np.sum(gO * E)) < 1e-6 * max(1.0, abs(fd))
+
+
 def test_augmented_residual_of_exact_solution_is_zero():
     p = S.make_problem(G=3, M=12, n_i=[2, 3, 2], k=2, seed=51, omega="chol")
     w, b = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
