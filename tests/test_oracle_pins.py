@@ -313,6 +313,26 @@ def test_kron_gradient_finite_differences_medium():
         assert abs(fd - np.sum(gO * E)) < 1e-6 * max(1.0, abs(fd))
 
 
+def test_refined_solution_matches_dense_and_converges():
+    # extended-precision refinement: equal to the dense brute force on tiny
+    # inputs; the corrections fall to the float64 rounding level
+    p = S.make_problem(G=4, M=9, n_i=[2, 3, 1, 2], k=2, seed=48, omega="chol")
+    gb = S.rng(49).standard_normal((p.n, 2))
+    out = O.sur_gls_refined(p.X_blocks, p.Omega, p.Y, gb, steps=3)
+    w_d, b_d = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
+    lam_d, gO_d = O.sur_gls_gradient(p.X_blocks, p.Omega, p.Y, gb)
+    assert rel(out["b"], b_d) < 1e-12 and rel(out["w"], w_d) < 1e-11
+    assert rel(out["lam"], lam_d) < 1e-11 and rel(out["dOmega"], gO_d) < 1e-11
+    # an ill-conditioned Omega (G = 128, cond ~ 5e6): the first correction is
+    # the normal equations' error, the later ones settle below 1e-15
+    q, Lf, _ = S.config4(M=20, G=128, nmin=2, nmax=4)
+    assert np.linalg.cond(q.Omega) > 1e6
+    out = O.sur_gls_refined(q.X_blocks, q.Omega, q.Y, steps=3)
+    c = out["corrections"][0]
+    assert c[1] > 1e-12 and c[-1] < 1e-15 and c[-2] < 1e-15, c
+    assert rel(out["b"], O.gls_formula(q.X_blocks, q.Omega, q.Y)) < 1e-8
+
+
 def test_augmented_residual_of_exact_solution_is_zero():
     p = S.make_problem(G=3, M=12, n_i=[2, 3, 2], k=2, seed=51, omega="chol")
     w, b = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
