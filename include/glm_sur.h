@@ -160,6 +160,33 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
                                         int64_t ldd, int k, double* b, int64_t ldb, int* iters,
                                         double* relres, glm_sur_stream_t stream);
 
+/*
+ * glm_sur_backward -- adjoint of the last glm_sur_solve for a loss L(b).
+ * K = [[Sigma, X], [X^T, 0]] of eq. (aug1) is symmetric, so with
+ * (lam; mu) = K^-1 (0; dL/db):  dL/dy = lam  and  dL/dK = -(lam; mu)(w; b)^T,
+ * whose Sigma part gives dL/domega_ab = -sum_t Lam[t, a] W[t, b] (M x G
+ * matrices of lam and of the forward w, summed over the k right-hand sides).
+ * lam = lam_1 + lam_2: lam_1 = Q_i R_i^-T (dL/db)_i meets X^T lam_1 = dL/db,
+ * and lam_2 is the w of eq. (aug1) for y' = -Sigma lam_1, found by the same
+ * PCG-Aug iteration (Algorithm glmpcg2) and precision as the forward solve.
+ * Only the forward's converged w is needed: no iterate is stored.
+ *   dL_db     : DEVICE, n x k column-major, ldg >= n.
+ *   dL_dY     : DEVICE output (nullable), m x k column-major, ldy >= m:
+ *               dL/dy per right-hand side, same layout as Y of glm_sur_solve.
+ *   dL_dOmega : DEVICE output (nullable), G x G column-major, ldo >= G:
+ *               (G_Omega + G_Omega^T) / 2, the gradient with respect to a
+ *               symmetric Omega, summed over the right-hand sides.
+ *   iters, relres : DEVICE outputs (nullable, k): of the adjoint solve.
+ * k must equal the k of the last solve; the handle must have no
+ * restrictions and Omega must not have changed since that solve
+ * (GLM_SUR_INVALID_ARG otherwise).  Afterwards glm_sur_get_status reports the
+ * adjoint solve, and glm_sur_get_w still returns the forward w, so the call
+ * may be repeated with another dL/db.
+ */
+glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY,
+                                int64_t ldy, double* dL_dOmega, int64_t ldo, int* iters, double* relres,
+                                glm_sur_stream_t stream);
+
 /* Synchronises and copies the per-column status of the last solve (k values,
  * glm_sur_status codes) into the HOST array `status`. */
 glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k);

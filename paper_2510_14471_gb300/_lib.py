@@ -50,6 +50,7 @@ SIGNATURES = {
     "glm_sur_get_status": (_I, [_VP, ctypes.POINTER(_I), _I]),
     "glm_sur_set_restrictions": (_I, [_VP, _VP, _I64, _I, _VP]),
     "glm_sur_solve_restricted": (_I, [_VP, _VP, _I64, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
+    "glm_sur_backward": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_get_w": (_I, [_VP, _VP, _I64, _VP]),
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
     "glm_sur_destroy": (None, [_VP]),
@@ -139,6 +140,12 @@ def glm_sur_solve_restricted(h: int, Y_ptr: int, ldy: int, d_ptr: int, ldd: int,
                              iters_ptr: int, relres_ptr: int, stream: int) -> None:
     check(lib().glm_sur_solve_restricted(h, Y_ptr, ldy, d_ptr, ldd, k, b_ptr, ldb, iters_ptr, relres_ptr, stream),
           "glm_sur_solve_restricted")
+
+
+def glm_sur_backward(h: int, g_ptr: int, ldg: int, k: int, dy_ptr: int, ldy: int, dom_ptr: int, ldo: int,
+                     iters_ptr: int, relres_ptr: int, stream: int) -> None:
+    check(lib().glm_sur_backward(h, g_ptr, ldg, k, dy_ptr, ldy, dom_ptr, ldo, iters_ptr, relres_ptr, stream),
+          "glm_sur_backward")
 
 
 def glm_sur_get_status(h: int, k: int):

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "adjoint.h"
 #include "glm_sur.h"
 #include "internal.h"
 #include "noalloc.h"
@@ -104,13 +105,25 @@ struct glm_sur_ctx {
   double* fbuf = nullptr;      // n' x k f_i = R_i c_i
   double* gC = nullptr;        // kc x k restriction rows of g
   int rcap = 0;                // k capacity of cbuf / fbuf / gC
+  bool w_restricted = false;   // w64 came from a restricted solve
+  // adjoint (glm_sur_backward)
+  double* wfwd = nullptr;      // the forward w while the adjoint solve runs
+  double* lam1 = nullptr;      // particular solution lam_1 = Q R^-T dL/db
+  double* opart = nullptr;     // chunk partials of the Omega gradient
+  int acap = 0;                // k capacity of wfwd / lam1
+  int64_t ocap = 0;            // doubles in opart
 };
 
 namespace {
 
 constexpr int kStateDoubles = 10;
 constexpr int kStateInts = 6;
-constexpr int kInnerStagnation = 25;   // stagnation window of the float32 inner solves
+// stagnation window of the float32 inner solves (at least; a longer outer
+// window W applies to them too)
+constexpr int kInnerStagnation = 25;
+
+// float64 PCG steps rather than float32 inner runs inside refinement
+bool fp64_steps(const glm_sur_opts& o) { return o.precision != GLM_SUR_PREC_FP32_REFINE; }
 
 glm_sur_status validate_opts(const glm_sur_opts* o) {
   if (o->precision != GLM_SUR_PREC_FP64 && o->precision != GLM_SUR_PREC_FP32_REFINE) return GLM_SUR_INVALID_ARG;
@@ -250,7 +263,7 @@ glm_sur_status ensure_workspace(glm_sur_ctx* h, int k) {
   GS_CUDA_TRY(dalloc(&h->w64, mk));
   GS_CUDA_TRY(dalloc(&h->g64, mk));
   GS_CUDA_TRY(dalloc(&h->E64, mk));
-  if (h->opts.precision == GLM_SUR_PREC_FP64) {
+  if (fp64_steps(h->opts)) {
     GS_CUDA_TRY(dalloc(&h->u64, mk));
     GS_CUDA_TRY(dalloc(&h->S64, mk));
     GS_CUDA_TRY(dalloc(&h->wb64, mk));
@@ -697,36 +710,38 @@ glm_sur_status ensure_restriction_workspace(glm_sur_ctx* h, int k) {
   return GLM_SUR_OK;
 }
 
-glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
-                          int64_t ldb, int* iters, double* relres, cudaStream_t s) {
-  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
-  const Geom& gm = h->gm;
-  const int64_t m = gm.M * gm.G;
-  if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
-  if (h->kc > 0 && (h->opts.precision != GLM_SUR_PREC_FP64 || (d && ldd < h->kc))) return GLM_SUR_INVALID_ARG;
+// Workspace and iteration plans for k right-hand sides; p64 receives the
+// float64 plan of the residual and recovery passes.
+glm_sur_status prepare_solve(glm_sur_t h, int k, IterPlan& p64) {
   glm_sur_status rc = ensure_workspace(h, k);
   if (rc != GLM_SUR_OK) return rc;
   rc = ensure_restriction_workspace(h, k);
   if (rc != GLM_SUR_OK) return rc;
-  const bool fp64 = h->opts.precision == GLM_SUR_PREC_FP64;
-  IterPlan p64;
   rc = make_plan(h, k, true, p64);
   if (rc != GLM_SUR_OK) return rc;
   if (h->plan_k != k || h->plan_prec != h->opts.precision) {
     IterPlan pit;
-    rc = make_plan(h, k, fp64, pit);
+    rc = make_plan(h, k, fp64_steps(h->opts), pit);
     if (rc != GLM_SUR_OK) return rc;
     h->plan = pit;
     h->plan_k = k;
     h->plan_prec = h->opts.precision;
     h->graph.reset();
   }
+  return GLM_SUR_OK;
+}
+
+// PCG-Aug (float64, or float32 inside float64 refinement) on the right-hand
+// sides already in y64; b = R^-1 Q^T (y - Sigma w) unless b is null.
+glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int64_t ldd, int k, double* b,
+                          int64_t ldb, int* iters, double* relres, cudaStream_t s) {
+  glm_sur_status rc = GLM_SUR_OK;
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G;
+  const bool fp64 = fp64_steps(h->opts);
   const int64_t mk = m * k;
   const int maxit = h->opts.maxit > 0 ? h->opts.maxit : (int)std::min<int64_t>(m - gm.n + 1, 1 << 30);
   GS_CUDA_TRY(cudaMemsetAsync(h->st.err, 0, sizeof(int), s));
-  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
-  h->launches += 1;
-  GS_CUDA_TRY(cudaGetLastError());
   h->last_k = k;
   if (fp64) {
     rc = reset_state(h, k, h->opts.tol, maxit, h->opts.stagnation_window, s);
@@ -790,9 +805,9 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
       GS_CUDA_TRY(cudaStreamSynchronize(s));
       if (all_done) break;
       // inner float32 PCG on P Sigma_e d = rho (live columns)
-      rc = reset_state(h, k, h->opts.inner_tol, maxit, kInnerStagnation, s);
+      rc = reset_state(h, k, h->opts.inner_tol, maxit, std::max(kInnerStagnation, h->opts.stagnation_window), s);
       if (rc != GLM_SUR_OK) return rc;
-      launch_init_inner(h->plan, gm, k, h->g64, h->d_mask, h->g32, h->u32, h->w32, h->cpart, s);
+      launch_init_inner<float>(h->plan, gm, k, h->g64, h->d_mask, h->g32, h->u32, h->w32, h->cpart, s);
       GS_CUDA_TRY(cudaMemsetAsync(h->wb32, 0, mk * sizeof(float), s));
       h->launches += 1;
       GS_CUDA_TRY(cudaGetLastError());
@@ -818,9 +833,51 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
     GS_CUDA_TRY(cudaStreamSynchronize(s));
   }
   if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, h->d_iters_acc, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  rc = recover_b(h, k, p64, b, ldb, s, d, ldd);
+  if (b) {
+    rc = recover_b(h, k, p64, b, ldb, s, d, ldd);
+    if (rc != GLM_SUR_OK) return rc;
+  }
+  return GLM_SUR_OK;
+}
+
+glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
+                          int64_t ldb, int* iters, double* relres, cudaStream_t s) {
+  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G;
+  if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
+  if (h->kc > 0 && (h->opts.precision != GLM_SUR_PREC_FP64 || (d && ldd < h->kc))) return GLM_SUR_INVALID_ARG;
+  IterPlan p64;
+  glm_sur_status rc = prepare_solve(h, k, p64);
+  if (rc != GLM_SUR_OK) return rc;
+  h->has_w = false;
+  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
+  h->launches += 1;
+  GS_CUDA_TRY(cudaGetLastError());
+  rc = solve_core(h, p64, d, ldd, k, b, ldb, iters, relres, s);
   if (rc != GLM_SUR_OK) return rc;
   h->has_w = true;
+  h->w_restricted = h->kc > 0;
+  return GLM_SUR_OK;
+}
+
+// Buffers of the adjoint: the saved forward w, lam_1 and the Omega-gradient partials.
+glm_sur_status ensure_adjoint_workspace(glm_sur_ctx* h, int k, int nch) {
+  const size_t mk = (size_t)h->gm.M * h->gm.G * k;
+  if (k > h->acap) {
+    dfree(h->wfwd); dfree(h->lam1);
+    h->acap = 0;
+    GS_CUDA_TRY(dalloc(&h->wfwd, mk));
+    GS_CUDA_TRY(dalloc(&h->lam1, mk));
+    h->acap = k;
+  }
+  const int64_t need = (int64_t)nch * h->gm.G * h->gm.G;
+  if (need > h->ocap) {
+    dfree(h->opart);
+    h->ocap = 0;
+    GS_CUDA_TRY(dalloc(&h->opart, (size_t)need));
+    h->ocap = need;
+  }
   return GLM_SUR_OK;
 }
 
@@ -840,12 +897,57 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
   return solve_impl(h, Y, ldy, d, ldd, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
 }
 
+glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY, int64_t ldy,
+                                double* dL_dOmega, int64_t ldo, int* iters, double* relres, glm_sur_stream_t stream) {
+  if (!h || !dL_db || (!dL_dY && !dL_dOmega)) return GLM_SUR_INVALID_ARG;
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G;
+  if (k < 1 || k != h->last_k || !h->has_w || h->w_restricted || h->kc > 0 || ldg < gm.n || (dL_dY && ldy < m) || (dL_dOmega && ldo < gm.G))
+    return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  IterPlan p64;
+  glm_sur_status rc = prepare_solve(h, k, p64);
+  if (rc != GLM_SUR_OK) return rc;
+  const int nch = adj_omega_chunks(gm, k, h->sms);
+  rc = ensure_adjoint_workspace(h, k, nch);
+  if (rc != GLM_SUR_OK) return rc;
+  const int64_t mk = m * k;
+  GS_CUDA_TRY(cudaMemcpyAsync(h->wfwd, h->w64, mk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // lam_1 = Q R^-T dL/db: block by block X_i^T lam_1 = R_i^T Q_i^T Q_i R_i^-T g_i = g_i
+  launch_adj_seed(gm, k, h->R, dL_db, ldg, h->C64, s);
+  GS_CUDA_TRY(cudaMemsetAsync(h->E64, 0, mk * sizeof(double), s));
+  launch_proj_update<double>(p64, gm, k, h->Q64, h->E64, h->lam1, h->C64, 0, nullptr, 1.0, h->cpart, h->st, 0, s);
+  // y' = 0 - Sigma lam_1; the remaining lam_2 solves eq. (aug1) for y'
+  launch_sigma_resid<double>(p64, gm, k, h->Om64, h->E64, h->lam1, h->y64, s);
+  h->launches += 3;
+  GS_CUDA_TRY(cudaGetLastError());
+  h->has_w = false;
+  rc = solve_core(h, p64, nullptr, 0, k, nullptr, 0, iters, relres, s);
+  if (rc != GLM_SUR_OK) return rc;
+  // lam = lam_1 + lam_2 (into w64), outputs, then the forward w back in place
+  launch_add_to_f64<double>(mk, h->lam1, h->w64, s);
+  h->launches += 1;
+  if (dL_dY) {
+    launch_layout_to_colmajor<double>(gm, k, h->w64, dL_dY, ldy, s);
+    h->launches += 1;
+  }
+  if (dL_dOmega) {
+    launch_adj_omega(gm, k, h->w64, h->wfwd, h->opart, nch, dL_dOmega, ldo, s);
+    h->launches += 2;
+  }
+  GS_CUDA_TRY(cudaMemcpyAsync(h->w64, h->wfwd, mk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  GS_CUDA_TRY(cudaGetLastError());
+  h->has_w = true;
+  return GLM_SUR_OK;
+}
+
 glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ldc, int kc, glm_sur_stream_t stream) {
   if (!h || kc < 0 || (kc > 0 && (!C || ldc < kc))) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const Geom& gm = h->gm;
   if (kc > 0 && (size_t)gm.n * sizeof(double) > 200 * 1024) return GLM_SUR_INVALID_ARG;   // n <= 25600
   dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
+  dfree(h->wfwd); dfree(h->lam1); dfree(h->opart);
   h->rcap = 0;
   h->kc = 0;
   h->plan_k = -1;
@@ -912,11 +1014,11 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
   if (!h || !ms || reps < 1 || h->last_k < 1 || h->plan_k != h->last_k) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int k = h->last_k;
-  const bool fp64 = h->opts.precision == GLM_SUR_PREC_FP64;
+  const bool fp64 = fp64_steps(h->opts);
   glm_sur_status rc = reset_state(h, k, 0.0, 1 << 30, 0, s);   // no stop tests
   if (rc != GLM_SUR_OK) return rc;
   if (fp64) rc = pcg_init<double>(h, k, h->y64, s);
-  else launch_init_inner(h->plan, h->gm, k, h->y64, nullptr, h->g32, h->u32, h->w32, h->cpart, s);
+  else launch_init_inner<float>(h->plan, h->gm, k, h->y64, nullptr, h->g32, h->u32, h->w32, h->cpart, s);
   cudaEvent_t ev[5];
   for (auto& e : ev) cudaEventCreate(&e);
   double acc[5] = {0, 0, 0, 0, 0};
@@ -990,6 +1092,7 @@ void glm_sur_destroy(glm_sur_t h) {
   dfree(h->gm.d_n_i); dfree(h->gm.d_off); dfree(h->gm.d_poff); dfree(h->gm.d_quad_blk); dfree(h->gm.d_r_off);
   dfree(h->gm.d_ug_blk0); dfree(h->gm.d_col_blk);
   dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
+  dfree(h->wfwd); dfree(h->lam1); dfree(h->opart);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);

@@ -1047,17 +1047,19 @@ __global__ void k_add_to_f64(int64_t n, const Tin* __restrict__ d, double* __res
     w[e] += (double)d[e];
 }
 
-// inner start of a refinement step: g32 = -(float)rho, u32 = w32 = 0, partials of g32^T g32
+// start of a refinement run: g = -(T)rho on live columns (0 elsewhere), u = 0,
+// w = 0 unless w is null (a float64 restart keeps its w), partials of g^T g
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_init_inner(int64_t M, int Gk, int k, const double* __restrict__ rho, const int* __restrict__ live, float* g,
-             float* u, float* w, double* __restrict__ cpart) {
+k_init_inner(int64_t M, int Gk, int k, const double* __restrict__ rho, const int* __restrict__ live, T* g, T* u,
+             T* w, double* __restrict__ cpart) {
   __shared__ double red[8 * kMaxRhs];
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
   const int64_t e0 = r0 * Gk, e1 = r1 * Gk;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    g[e] = (live == nullptr || live[e % k]) ? (float)(-rho[e]) : 0.f;
-    u[e] = 0.f;
-    w[e] = 0.f;
+    g[e] = (live == nullptr || live[e % k]) ? (T)(-rho[e]) : (T)0;
+    u[e] = (T)0;
+    if (w) w[e] = (T)0;
   }
   __syncthreads();
   // second pass for the per-column sums (k <= 64): warp w sums column j = w, w+8, ...
@@ -1297,10 +1299,15 @@ void launch_add_to_f64(int64_t n, const Tin* d, double* w, cudaStream_t s) {
 }
 template void launch_add_to_f64<float>(int64_t, const float*, double*, cudaStream_t);
 template void launch_add_to_f64<double>(int64_t, const double*, double*, cudaStream_t);
-void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, float* g,
-                       float* u, float* w, double* cpart, cudaStream_t s) {
-  k_init_inner<<<p.n_cpart, 256, 0, s>>>(gm.M, gm.G * k, k, rho, live, g, u, w, cpart);
+template <typename T>
+void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, T* g, T* u,
+                       T* w, double* cpart, cudaStream_t s) {
+  k_init_inner<T><<<p.n_cpart, 256, 0, s>>>(gm.M, gm.G * k, k, rho, live, g, u, w, cpart);
 }
+template void launch_init_inner<float>(const IterPlan&, const Geom&, int, const double*, const int*, float*, float*,
+                                       float*, double*, cudaStream_t);
+template void launch_init_inner<double>(const IterPlan&, const Geom&, int, const double*, const int*, double*,
+                                        double*, double*, double*, cudaStream_t);
 template <typename T>
 void launch_colsumsq(const IterPlan& p, const Geom& gm, int k, const T* v, double* part, cudaStream_t s) {
   k_colsumsq<T><<<p.n_cpart, 256, 0, s>>>(gm.M, gm.G * k, k, v, part);

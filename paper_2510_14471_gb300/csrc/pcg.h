@@ -64,8 +64,9 @@ template <typename Tin, typename Tout>
 void launch_convert(int64_t n, const Tin* in, Tout* out, double scale, cudaStream_t s);
 template <typename Tin>
 void launch_add_to_f64(int64_t n, const Tin* d, double* w, cudaStream_t s);
-void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, float* g,
-                       float* u, float* w, double* cpart, cudaStream_t s);
+template <typename T>
+void launch_init_inner(const IterPlan& p, const Geom& gm, int k, const double* rho, const int* live, T* g, T* u,
+                       T* w, double* cpart, cudaStream_t s);
 void launch_masked_axpy(int64_t n, int k, const int* mask, double sign, const double* d, double* w,
                         cudaStream_t s);
 template <typename T>

@@ -50,6 +50,7 @@ class GlmSur:
         self.opts.max_refine = max_refine
         self.opts.chunk = chunk
         self.opts.inner_shift = inner_shift
+        self.generation = 0     # number of solves so far (the adjoint belongs to the last one)
         self._h = L.glm_sur_setup(self.G, self.M, self.n_i, self._X.data_ptr(), self.M, self._Omega.data_ptr(),
                                   self.opts, self._stream())
 
@@ -105,7 +106,29 @@ class GlmSur:
             L.glm_sur_solve(self._h, Ycm.data_ptr(), m, k, b.data_ptr(), self.n, iters.data_ptr(),
                             relres.data_ptr(), self._stream())
         status = L.glm_sur_get_status(self._h, k)
+        self.generation += 1
         return SolveResult(b.t(), iters, relres, status)
+
+    def backward(self, dL_db, want_y: bool = True, want_omega: bool = True):
+        """Adjoint of the last solve (same k, no restrictions, Omega unchanged).
+        dL_db: (n, k) or (n,).  Returns (dL_dY (m, k) or None, dL_dOmega (G, G)
+        symmetrised or None, iters, relres, status) of the adjoint solve."""
+        g = _dev_f64(dL_db, self.device)
+        if g.dim() == 1:
+            g = g[:, None]
+        k = g.shape[1]
+        gcm = g.t().contiguous()
+        m = self.M * self.G
+        dY = torch.empty((k, m), dtype=torch.float64, device=self.device) if want_y else None
+        dO = torch.empty((self.G, self.G), dtype=torch.float64, device=self.device) if want_omega else None
+        iters = torch.zeros(k, dtype=torch.int32, device=self.device)
+        relres = torch.zeros(k, dtype=torch.float64, device=self.device)
+        L.glm_sur_backward(self._h, gcm.data_ptr(), self.n, k, dY.data_ptr() if want_y else 0, m,
+                           dO.data_ptr() if want_omega else 0, self.G, iters.data_ptr(), relres.data_ptr(),
+                           self._stream())
+        status = L.glm_sur_get_status(self._h, k)
+        # dO is written column-major; it is symmetric, so its transpose is itself
+        return (dY.t() if want_y else None), dO, iters, relres, status
 
     def w(self, k: int) -> torch.Tensor:
         out = torch.empty((k, self.M * self.G), dtype=torch.float64, device=self.device)
@@ -198,3 +221,36 @@ class GlmSurBatch:
             self.close()
         except Exception:
             pass
+
+
+class SurGLSFunction(torch.autograd.Function):
+    """b = GLS estimate of the SUR model of ``solver`` (its X_i) for responses
+    Y (m, k) and covariance Omega (G, G, symmetric), differentiable in Y and
+    Omega through ``GlmSur.backward``.  Usage: SurGLSFunction.apply(Y, Omega,
+    solver).  The backward pass must run before the solver's next solve."""
+
+    @staticmethod
+    def forward(ctx, Y, Omega, solver):
+        solver.set_omega(Omega.detach())
+        r = solver.solve(Y.detach())
+        bad = [s for s in r.status if s not in (L.GLM_SUR_OK, L.GLM_SUR_STAGNATED)]
+        if bad:
+            raise RuntimeError(f"forward solve ended with status {bad}")
+        ctx.solver, ctx.token, ctx.vec = solver, solver.generation, Y.dim() == 1
+        return r.b[:, 0] if ctx.vec else r.b
+
+    @staticmethod
+    def backward(ctx, gb):
+        solver = ctx.solver
+        if solver.generation != ctx.token:
+            raise RuntimeError("the solver ran another solve after this forward; its w is gone")
+        need_y, need_om = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_y or need_om):
+            return None, None, None
+        dY, dO, _, _, status = solver.backward(gb, want_y=need_y, want_omega=need_om)
+        bad = [s for s in status if s not in (L.GLM_SUR_OK, L.GLM_SUR_STAGNATED)]
+        if bad:
+            raise RuntimeError(f"adjoint solve ended with status {bad}")
+        if dY is not None and ctx.vec:
+            dY = dY[:, 0]
+        return dY, dO, None
