@@ -290,6 +290,11 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
 /* Synchronises; HOST status (count x k); returns the first status other than
  * GLM_SUR_OK / GLM_SUR_STAGNATED. */
 glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status);
+/* Work of the last batch solve, per instance (HOST arrays of count, either
+ * nullable): float32 PCG steps its CTA ran over all refinement rounds (the
+ * unit of the per-step traffic), and SM clock cycles from its start to its
+ * end.  Synchronises. */
+glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* cycles);
 /* Tile height chosen by the autotuner (0 before the first solve); tune_ms
  * (HOST, 3, nullable) receives the timed candidates (8, 16, 32 rows). */
 int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms);

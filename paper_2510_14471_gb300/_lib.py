@@ -62,6 +62,7 @@ SIGNATURES = {
     "glm_sur_batch_get_setup_status": (_I, [_VP]),
     "glm_sur_batch_solve": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
     "glm_sur_batch_get_status": (_I, [_VP, ctypes.POINTER(_I)]),
+    "glm_sur_batch_get_work": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
     "glm_sur_batch_tile": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "glm_sur_batch_launch_count": (ctypes.c_int64, [_VP]),
     "glm_sur_batch_destroy": (None, [_VP]),
@@ -211,6 +212,13 @@ def glm_sur_batch_get_status(h: int, n: int):
     if rc in (GLM_SUR_INVALID_ARG, GLM_SUR_CUDA_ERROR):
         check(rc, "glm_sur_batch_get_status")
     return [int(v) for v in arr]
+
+
+def glm_sur_batch_get_work(h: int, count: int):
+    steps = (_I * count)()
+    cycles = (ctypes.c_longlong * count)()
+    check(lib().glm_sur_batch_get_work(h, steps, cycles), "glm_sur_batch_get_work")
+    return [int(v) for v in steps], [int(v) for v in cycles]
 
 
 def glm_sur_batch_tile(h: int):

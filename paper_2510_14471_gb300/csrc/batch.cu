@@ -36,6 +36,7 @@ struct Smem {
   float* tile32;   // 2 x kTR x G x K
   double* e64;     // np x K
   float* e32;      // np x K
+  void* qtile;     // kTR x np rows of Q (float64 or float32), staged per row tile
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -48,6 +49,7 @@ __host__ __device__ inline size_t smem_bytes(int K, int kTR, int maxG, int maxNp
   b += align16(sizeof(double) * (kBT / 32) * K) + align16(sizeof(double) * 4 * K);
   b += align16(sizeof(double) * kTR * maxG * K) + align16(sizeof(float) * 2 * kTR * maxG * K);
   b += align16(sizeof(double) * maxNp * K) + align16(sizeof(float) * maxNp * K);
+  b += align16(sizeof(double) * kTR * maxNp);
   return b;
 }
 
@@ -65,7 +67,8 @@ __device__ inline Smem carve(unsigned char* base, int K, int kTR, int maxG, int 
   s.tile64 = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * kTR * maxG * K);
   s.tile32 = reinterpret_cast<float*>(base + o); o += align16(sizeof(float) * 2 * kTR * maxG * K);
   s.e64 = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * maxNp * K);
-  s.e32 = reinterpret_cast<float*>(base + o);
+  s.e32 = reinterpret_cast<float*>(base + o); o += align16(sizeof(float) * maxNp * K);
+  s.qtile = base + o;
   return s;
 }
 
@@ -88,6 +91,65 @@ __device__ void cta_sum_strided(double v, double* red, double* out) {
   __syncthreads();
 }
 
+// dst[0..n) = src[0..n) (float32 row tile of a (M, G, K) vector; all
+// threads, four vector loads per thread issued before their stores).  With
+// K a multiple of 4 every row tile starts on a 16-byte boundary and moves as
+// float4, else as scalars.
+template <int K>
+__device__ __forceinline__ void copy_tile(const float* __restrict__ src, float* __restrict__ dst, int n) {
+  if constexpr (K % 4 == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const int n4 = n >> 2;
+    int e = threadIdx.x;
+    for (; e + 3 * kBT < n4; e += 4 * kBT) {
+      const float4 a = __ldcg(s4 + e), b = __ldcg(s4 + e + kBT), c = __ldcg(s4 + e + 2 * kBT),
+                   d = __ldcg(s4 + e + 3 * kBT);
+      d4[e] = a; d4[e + kBT] = b; d4[e + 2 * kBT] = c; d4[e + 3 * kBT] = d;
+    }
+    for (; e < n4; e += kBT) d4[e] = __ldcg(s4 + e);
+  } else {
+    int e = threadIdx.x;
+    for (; e + 3 * kBT < n; e += 4 * kBT) {
+      const float a = __ldcg(src + e), b = __ldcg(src + e + kBT), c = __ldcg(src + e + 2 * kBT),
+                  d = __ldcg(src + e + 3 * kBT);
+      dst[e] = a; dst[e + kBT] = b; dst[e + 2 * kBT] = c; dst[e + 3 * kBT] = d;
+    }
+    for (; e < n; e += kBT) dst[e] = __ldcg(src + e);
+  }
+}
+
+// S[e] = sum_g U[r, g, j] Omega[g, h] for the elements e = (r G + h) K + j
+// of a row tile (tr rows), four elements per thread in flight; calls
+// epi(e, r, h, j, S[e]) for each.  U and S may be float or double.
+template <int K, typename T, typename Epi>
+__device__ __forceinline__ void sigma_rows(const T* __restrict__ U, int tr, int G, int Gq, const T* __restrict__ om,
+                                           Epi epi) {
+  const int n = tr * G * K;
+  for (int e0 = threadIdx.x; e0 < n; e0 += 4 * kBT) {
+    int ub[4], hh[4];
+    T sv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int e = e0 + a * kBT < n ? e0 + a * kBT : e0;
+      const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
+      ub[a] = r * G * K + j;
+      hh[a] = h;
+      sv[a] = (T)0;
+    }
+    for (int g = 0; g < G; ++g) {
+      const T* om_g = om + g * Gq;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) sv[a] += U[ub[a] + g * K] * om_g[hh[a]];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int e = e0 + a * kBT;
+      if (e < n) epi(e, ub[a] / (G * K), hh[a], ub[a] % K, sv[a]);
+    }
+  }
+}
+
 // One instance, K right-hand sides, by one CTA.
 template <int K, int kTR>
 struct Inst {
@@ -98,10 +160,29 @@ struct Inst {
   __device__ int G() const { return d.G; }
   __device__ int64_t GK() const { return (int64_t)d.G * K; }
 
-  // Accumulate acc(pair) += sum_{rows of tile} Q[t, 4q+c] * tile[r][blk(q)][j]
-  // for the thread's (quad, column) pairs.
+  // Copy rows t0 .. t0+tr-1 of the instance's Q (np values each, 16-byte
+  // aligned rows) into the shared tile Qt, all threads together.
+  template <typename TQ>
+  __device__ void stage_q(const TQ* Q, int64_t t0, int tr, TQ* Qt) const {
+    using V = typename Vec4<TQ>::type;
+    const V* src = reinterpret_cast<const V*>(Q + d.q_off + t0 * d.np);
+    V* dst = reinterpret_cast<V*>(Qt);
+    const int n = tr * d.nq;
+    int e = threadIdx.x;
+    for (; e + kBT < n; e += 2 * kBT) {
+      V a, b;
+      Vec4<TQ>::copy(src + e, &a);
+      Vec4<TQ>::copy(src + e + kBT, &b);
+      dst[e] = a;
+      dst[e + kBT] = b;
+    }
+    for (; e < n; e += kBT) Vec4<TQ>::copy(src + e, dst + e);
+  }
+
+  // Accumulate acc(pair) += sum_{rows of tile} Qt[r, 4q+c] * tile[r][blk(q)][j]
+  // for the thread's (quad, column) pairs (Qt: the staged rows of Q).
   template <typename TQ, typename TT, typename TA>
-  __device__ void accumulate(const TQ* Q, const TT* tile, int64_t t0, int tr, TA (&acc)[kPairsPerThread][4]) const {
+  __device__ void accumulate(const TQ* Qt, const TT* tile, int tr, TA (&acc)[kPairsPerThread][4]) const {
     const int npairs = d.nq * K;
 #pragma unroll
     for (int a = 0; a < kPairsPerThread; ++a) {
@@ -109,14 +190,26 @@ struct Inst {
       if (pr < npairs) {
         const int q = pr / K, j = pr % K;
         const int blk = P.quad_blk[d.quad0 + q];
+#pragma unroll 4
         for (int r = 0; r < tr; ++r) {
-          const TQ* qp = Q + d.q_off + (t0 + r) * d.np + 4 * q;
+          TQ qv[4];
+          Vec4<TQ>::load(Qt + r * d.np + 4 * q, qv);
           const TA sv = (TA)tile[((int64_t)r * d.G + blk) * K + j];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] += (TA)qp[c] * sv;
+          for (int c = 0; c < 4; ++c) acc[a][c] += (TA)qv[c] * sv;
         }
       }
     }
+  }
+
+  // (Q e)[row r of the staged tile, i, j] = sum over block i's columns
+  template <typename TQ, typename TE>
+  __device__ TE qe_tile(const TQ* Qt, const TE* e, int r, int i, int j) const {
+    const TQ* qp = Qt + r * d.np + sm.poff[i];
+    const TE* ep = e + sm.poff[i] * K + j;
+    TE s = 0;
+    for (int c = 0; c < sm.n_i[i]; ++c) s += (TE)qp[c] * ep[c * K];
+    return s;
   }
 
   // Write the accumulators to e (np x K) in shared memory.
@@ -152,10 +245,14 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
   float* tile32 = sm.tile32;
   double* e64 = sm.e64;
   float* e32 = sm.e32;
+  double* qt64 = reinterpret_cast<double*>(sm.qtile);
+  float* qt32 = reinterpret_cast<float*>(sm.qtile);
   const int G = dsc.G, Gq = dsc.Gq;
   const int64_t M = dsc.M, GK = (int64_t)G * K;
   const int64_t nv = M * GK;
   const int tid = threadIdx.x;
+  const long long clk0 = clock64();
+  int cta_steps = 0;
   // instance constants in shared memory
   for (int e = tid; e < G * Gq; e += kBT) {
     sm.om64[e] = P.om64[dsc.om_off + e];
@@ -187,17 +284,14 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
     double acc64[kPairsPerThread][4] = {};
     for (int64_t t0 = 0; t0 < M; t0 += kTR) {
       const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
-      for (int e = tid; e < tr * GK; e += kBT) {
-        const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
-        const int64_t t = t0 + r;
-        double s = 0.0;
-        for (int gg = 0; gg < G; ++gg) s += w64[(t * G + gg) * K + j] * sm.om64[gg * Gq + h];
-        const double ev = Y[(int64_t)j * m + (int64_t)h * M + t] - s;
+      sigma_rows<K>(w64 + t0 * GK, tr, G, Gq, sm.om64, [&](int e, int r, int h, int j, double sv) {
+        const double ev = Y[(int64_t)j * m + (int64_t)h * M + t0 + r] - sv;
         tile64[e] = ev;
-        E64[t * GK + h * K + j] = ev;
-      }
+        E64[t0 * GK + e] = ev;
+      });
+      I.stage_q(P.q64, t0, tr, qt64);
       __syncthreads();
-      I.accumulate(P.q64, tile64, t0, tr, acc64);
+      I.accumulate(qt64, tile64, tr, acc64);
       __syncthreads();
     }
     I.store_acc(acc64, e64);
@@ -249,133 +343,145 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
       w32[e] = 0.f;
       wb32[e] = 0.f;
     }
-    double c1[K], c[K], cbest[K], csnap[K], cstop[K];
-    int ibest[K], act[K], it_done[K], snap[K], conv[K];
+    // Per-column state of the inner solve.  It is the same for every thread,
+    // so it lives in shared memory, written by thread j < K between barriers.
+    __shared__ double s_c1[K], s_c[K], s_cbest[K], s_csnap[K], s_cstop[K], s_mu[K], s_lam[K];
+    __shared__ int s_ibest[K], s_act[K], s_done[K], s_snap[K], s_conv[K];
     {
       double cs = 0.0;
       __syncthreads();
       for (int64_t e = tid; e < nv; e += kBT) cs += (double)g32[e] * (double)g32[e];
       cta_sum_strided<K>(cs, sm.red, sm.colv + K);
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        c1[j] = c[j] = cbest[j] = csnap[j] = cstop[j] = sm.colv[K + j];
-        ibest[j] = 0;
-        act[j] = (c1[j] > 0.0) && isfinite(c1[j]);
-        it_done[j] = 0;
-        snap[j] = 0;
-        conv[j] = 0;
+      if (tid < K) {
+        const double v = sm.colv[K + tid];
+        s_c1[tid] = s_c[tid] = s_cbest[tid] = s_csnap[tid] = s_cstop[tid] = v;
+        s_ibest[tid] = 0;
+        s_act[tid] = (v > 0.0) && isfinite(v);
+        s_done[tid] = 0;
+        s_snap[tid] = 0;
+        s_conv[tid] = 0;
+        s_mu[tid] = 0.0;
+        s_lam[tid] = 0.0;
       }
+      __syncthreads();
     }
-    double mu[K] = {};
     for (int it = 1; it <= o.inner_maxit; ++it) {
       int anyact = 0;
 #pragma unroll
-      for (int j = 0; j < K; ++j) anyact |= act[j];
+      for (int j = 0; j < K; ++j) anyact |= s_act[j];
       if (!anyact) break;
+      ++cta_steps;
       // pass A: u = g + mu u ; S = U Omega ; d = u.S ; e = Q^T S
       float acc32[kPairsPerThread][4] = {};
       double dd = 0.0;
       for (int64_t t0 = 0; t0 < M; t0 += kTR) {
         const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
+        float* gt = reinterpret_cast<float*>(tile64);   // g tile (tile64 is free in the inner solve)
+        copy_tile<K>(u32 + t0 * GK, tile32, tr * (int)GK);
+        copy_tile<K>(g32 + t0 * GK, gt, tr * (int)GK);
+        I.stage_q(P.q32, t0, tr, qt32);
+        __syncthreads();
         for (int e = tid; e < tr * GK; e += kBT) {
           const int j = e % K;
-          const int64_t gi = t0 * GK + e;
-          float un = u32[gi];
-          if (act[j]) {
-            un = g32[gi] + (float)mu[j] * un;
-            u32[gi] = un;
+          if (s_act[j]) {
+            const float un = gt[e] + (float)s_mu[j] * tile32[e];
+            tile32[e] = un;     // u tile
+            u32[t0 * GK + e] = un;
           }
-          tile32[e] = un;     // u tile
         }
         __syncthreads();
         // S tile into the second half of tile32, d partials
         float* St = tile32 + kTR * GK;
-        for (int e = tid; e < tr * GK; e += kBT) {
-          const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
-          float s = 0.f;
-          for (int gg = 0; gg < G; ++gg) s += tile32[(r * G + gg) * K + j] * sm.om32[gg * Gq + h];
-          St[e] = s;
-          dd += (double)(s * tile32[e]);
-        }
+        sigma_rows<K>(tile32, tr, G, Gq, sm.om32, [&](int e, int, int, int, float sv) {
+          St[e] = sv;
+          dd += (double)(sv * tile32[e]);
+        });
         __syncthreads();
-        I.accumulate(P.q32, St, t0, tr, acc32);
+        I.accumulate(qt32, St, tr, acc32);
         __syncthreads();
       }
       I.store_acc(acc32, e32);
       cta_sum_strided<K>(dd, sm.red, sm.colv + 2 * K);
-      double lam[K];
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const double dj = sm.colv[2 * K + j];
-        lam[j] = 0.0;
-        if (act[j]) {
-          if (!(dj > 0.0) || !isfinite(dj)) act[j] = 0;
-          else lam[j] = c[j] / dj;
+      if (tid < K) {
+        const double dj = sm.colv[2 * K + tid];
+        s_lam[tid] = 0.0;
+        if (s_act[tid]) {
+          if (!(dj > 0.0) || !isfinite(dj)) s_act[tid] = 0;
+          else s_lam[tid] = s_c[tid] / dj;
         }
       }
+      __syncthreads();
       // pass B: t = S - Q e ; g -= lam t ; w -= lam u ; c' = g.g
       double cn = 0.0;
       for (int64_t t0 = 0; t0 < M; t0 += kTR) {
         const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
-        for (int e = tid; e < tr * GK; e += kBT) tile32[e] = u32[t0 * GK + e];
+        float* gt = tile32 + kTR * GK;                  // g tile
+        float* wt = reinterpret_cast<float*>(tile64);   // w tile
+        copy_tile<K>(u32 + t0 * GK, tile32, tr * (int)GK);
+        copy_tile<K>(g32 + t0 * GK, gt, tr * (int)GK);
+        copy_tile<K>(w32 + t0 * GK, wt, tr * (int)GK);
+        I.stage_q(P.q32, t0, tr, qt32);
         __syncthreads();
-        for (int e = tid; e < tr * GK; e += kBT) {
-          const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
+        sigma_rows<K>(tile32, tr, G, Gq, sm.om32, [&](int e, int r, int h, int j, float sv) {
           const int64_t gi = t0 * GK + e;
-          float s = 0.f;
-          for (int gg = 0; gg < G; ++gg) s += tile32[(r * G + gg) * K + j] * sm.om32[gg * Gq + h];
-          const float tval = s - I.qe(P.q32, e32, t0 + r, h, j);
-          const float gn = g32[gi] - (float)lam[j] * tval;
+          const float lj = (float)s_lam[j];
+          const float tval = sv - I.qe_tile(qt32, e32, r, h, j);
+          const float gn = gt[e] - lj * tval;
           g32[gi] = gn;
-          const float wo = w32[gi];
-          if (snap[j]) wb32[gi] = wo;   // the w whose c was a new quarter-low
-          w32[gi] = wo - (float)lam[j] * tile32[e];
+          const float wo = wt[e];
+          if (s_snap[j]) wb32[gi] = wo;   // the w whose c was a new quarter-low
+          w32[gi] = wo - lj * tile32[e];
           cn += (double)(gn * gn);
-        }
+        });
         __syncthreads();
       }
       cta_sum_strided<K>(cn, sm.red, sm.colv + 3 * K);
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        snap[j] = 0;
-        if (!act[j]) { mu[j] = 0.0; continue; }
-        const double cj = sm.colv[3 * K + j];
-        it_done[j] = it;
-        cstop[j] = cj;
-        if (cj < cbest[j]) { cbest[j] = cj; ibest[j] = it; }
-        const bool done_conv = isfinite(cj) && cj >= 0.0 && sqrt(cj / c1[j]) <= o.inner_tol;
-        if (done_conv || !isfinite(cj) || cj < 0.0 || it - ibest[j] >= o.inner_window || it >= o.inner_maxit) {
-          act[j] = 0;
-          mu[j] = 0.0;
-          conv[j] = done_conv;
+      if (tid < K) {
+        const int j = tid;
+        s_snap[j] = 0;
+        if (!s_act[j]) {
+          s_mu[j] = 0.0;
         } else {
-          if (cj < 0.25 * csnap[j]) { csnap[j] = cj; snap[j] = 1; }   // saved in the next pass B
-          mu[j] = cj / c[j];
-          c[j] = cj;
+          const double cj = sm.colv[3 * K + j];
+          s_done[j] = it;
+          s_cstop[j] = cj;
+          if (cj < s_cbest[j]) { s_cbest[j] = cj; s_ibest[j] = it; }
+          const bool done_conv = isfinite(cj) && cj >= 0.0 && sqrt(cj / s_c1[j]) <= o.inner_tol;
+          if (done_conv || !isfinite(cj) || cj < 0.0 || it - s_ibest[j] >= o.inner_window || it >= o.inner_maxit) {
+            s_act[j] = 0;
+            s_mu[j] = 0.0;
+            s_conv[j] = done_conv;
+          } else {
+            if (cj < 0.25 * s_csnap[j]) { s_csnap[j] = cj; s_snap[j] = 1; }   // saved in the next pass B
+            s_mu[j] = cj / s_c[j];
+            s_c[j] = cj;
+          }
         }
       }
+      __syncthreads();
     }
     // columns that stopped without converging take their saved best w
     {
       int any_restore = 0;
 #pragma unroll
-      for (int j = 0; j < K; ++j) any_restore |= (!conv[j] && !(cstop[j] <= csnap[j]));
+      for (int j = 0; j < K; ++j) any_restore |= (!s_conv[j] && !(s_cstop[j] <= s_csnap[j]));
       if (any_restore) {
         for (int64_t e = tid; e < nv; e += kBT) {
           const int j = (int)(e % K);
-          if (!conv[j] && !(cstop[j] <= csnap[j])) w32[e] = wb32[e];
+          if (!s_conv[j] && !(s_cstop[j] <= s_csnap[j])) w32[e] = wb32[e];
         }
         __syncthreads();
       }
     }
-    if (tid < K) iters_acc[tid] += it_done[tid];
+    if (tid < K) iters_acc[tid] += s_done[tid];
     // ---- d = P (double) w32 ; w64 += d on the live columns
     double accp[kPairsPerThread][4] = {};
     for (int64_t t0 = 0; t0 < M; t0 += kTR) {
       const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
       for (int e = tid; e < tr * GK; e += kBT) tile64[e] = (double)w32[t0 * GK + e];
+      I.stage_q(P.q64, t0, tr, qt64);
       __syncthreads();
-      I.accumulate(P.q64, tile64, t0, tr, accp);
+      I.accumulate(qt64, tile64, tr, accp);
       __syncthreads();
     }
     I.store_acc(accp, e64);
@@ -393,15 +499,12 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
   double accb[kPairsPerThread][4] = {};
   for (int64_t t0 = 0; t0 < M; t0 += kTR) {
     const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
-    for (int e = tid; e < tr * GK; e += kBT) {
-      const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
-      const int64_t t = t0 + r;
-      double s = 0.0;
-      for (int gg = 0; gg < G; ++gg) s += w64[(t * G + gg) * K + j] * sm.om64[gg * Gq + h];
-      tile64[e] = Y[(int64_t)j * m + (int64_t)h * M + t] - s;
-    }
+    sigma_rows<K>(w64 + t0 * GK, tr, G, Gq, sm.om64, [&](int e, int r, int h, int j, double sv) {
+      tile64[e] = Y[(int64_t)j * m + (int64_t)h * M + t0 + r] - sv;
+    });
+    I.stage_q(P.q64, t0, tr, qt64);
     __syncthreads();
-    I.accumulate(P.q64, tile64, t0, tr, accb);
+    I.accumulate(qt64, tile64, tr, accb);
     __syncthreads();
   }
   I.store_acc(accb, e64);
@@ -425,6 +528,10 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
     P.status[(int64_t)dsc.index * K + tid] = fin[tid];
     P.iters[(int64_t)dsc.index * K + tid] = iters_acc[tid];
     P.relres[(int64_t)dsc.index * K + tid] = rrout[tid];
+  }
+  if (tid == 0) {
+    P.steps[dsc.index] = cta_steps;
+    P.cycles[dsc.index] = clock64() - clk0;
   }
   __syncthreads();
 }

@@ -41,6 +41,8 @@ struct BatchPools {
   int* status;
   int* iters;
   double* relres;
+  int* steps;                // per instance: float32 steps the CTA ran (all refinement rounds)
+  long long* cycles;         // per instance: SM clock cycles from start to end
 };
 
 struct BatchOpts {

@@ -30,8 +30,9 @@ struct glm_sur_batch_ctx {
   int kcap = 0;
   double *w64 = nullptr, *E64 = nullptr, *d64 = nullptr;
   float *g32 = nullptr, *u32 = nullptr, *w32 = nullptr, *wb32 = nullptr;
-  int *status = nullptr, *iters_d = nullptr, *counter = nullptr;
+  int *status = nullptr, *iters_d = nullptr, *counter = nullptr, *steps_d = nullptr;
   double* relres_d = nullptr;
+  long long* cycles_d = nullptr;
   BatchInst* d_insts = nullptr;
   int insts_k = 0;
   int last_k = 0;
@@ -59,7 +60,8 @@ void bfree(T*& p) {
 
 void free_solve(glm_sur_batch_ctx* h) {
   bfree(h->w64); bfree(h->E64); bfree(h->d64); bfree(h->g32); bfree(h->u32); bfree(h->w32); bfree(h->wb32);
-  bfree(h->status); bfree(h->iters_d); bfree(h->relres_d); bfree(h->d_insts);
+  bfree(h->status); bfree(h->iters_d); bfree(h->relres_d); bfree(h->d_insts); bfree(h->steps_d);
+  bfree(h->cycles_d);
   h->kcap = 0;
   h->insts_k = 0;
   if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -216,6 +218,8 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     GS_CUDA_TRY(balloc(&h->status, (size_t)h->count * k));
     GS_CUDA_TRY(balloc(&h->iters_d, (size_t)h->count * k));
     GS_CUDA_TRY(balloc(&h->relres_d, (size_t)h->count * k));
+    GS_CUDA_TRY(balloc(&h->steps_d, (size_t)h->count));
+    GS_CUDA_TRY(balloc(&h->cycles_d, (size_t)h->count));
     GS_CUDA_TRY(balloc(&h->d_insts, (size_t)h->count));
     h->kcap = k;
   }
@@ -254,7 +258,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
   }
   BatchPools P{h->q64, h->q32, h->R, h->om64, h->om32, h->d_n_i, h->d_poff, h->d_r_off, h->d_quad_blk,
                h->w64, h->E64, h->d64, h->g32, h->u32, h->w32, h->wb32, Y, b, h->status, h->iters_d,
-               h->relres_d};
+               h->relres_d, h->steps_d, h->cycles_d};
   BatchOpts bo{h->opts.tol, h->opts.inner_tol, h->opts.max_refine, 4000, 25};
   if (h->tile == 0) {
     // autotune: time one batch solve per tile height, keep the fastest
@@ -265,7 +269,10 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     for (int t = 0; t < 3; ++t) {
       const int TR = kBatchTiles[t];
       int ctas = 0;
-      GS_CUDA_TRY(batch_prepare(k, TR, h->maxG, h->maxNp, &ctas));
+      if (batch_prepare(k, TR, h->maxG, h->maxNp, &ctas) != cudaSuccess) {
+        cudaGetLastError();   // tile height whose shared memory does not fit
+        ctas = 0;
+      }
       if (ctas < 1) { h->tune_ms[t] = -1; continue; }
       const int grid = h->sms * ctas;
       cudaEventRecord(e0, s);
@@ -323,6 +330,15 @@ glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status) {
       worst = (glm_sur_status)status[j];
   }
   return worst;
+}
+
+glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* cycles) {
+  if (!h || (!steps && !cycles)) return GLM_SUR_INVALID_ARG;
+  if (!h->steps_d) return GLM_SUR_INVALID_ARG;   // no solve yet
+  GS_CUDA_TRY(cudaDeviceSynchronize());
+  if (steps) GS_CUDA_TRY(cudaMemcpy(steps, h->steps_d, sizeof(int) * h->count, cudaMemcpyDeviceToHost));
+  if (cycles) GS_CUDA_TRY(cudaMemcpy(cycles, h->cycles_d, sizeof(long long) * h->count, cudaMemcpyDeviceToHost));
+  return GLM_SUR_OK;
 }
 
 int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms) {

@@ -46,6 +46,8 @@ __host__ __device__ inline int round_up4(int x) { return (x + 3) & ~3; }
 // Vector load/store of 4 consecutive scalars (16 B for float, 2x16 B for double).
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
+  using type = float4;
+  __device__ __forceinline__ static void copy(const type* src, type* dst) { *dst = *src; }
   __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
     float4 t = *reinterpret_cast<const float4*>(p);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
@@ -56,6 +58,11 @@ template <> struct Vec4<float> {
   }
 };
 template <> struct Vec4<double> {
+  struct __align__(16) type { double2 a, b; };
+  __device__ __forceinline__ static void copy(const type* src, type* dst) {
+    dst->a = src->a;
+    dst->b = src->b;
+  }
   __device__ __forceinline__ static void load(const double* p, double (&v)[4]) {
     double2 a = reinterpret_cast<const double2*>(p)[0];
     double2 b = reinterpret_cast<const double2*>(p)[1];
