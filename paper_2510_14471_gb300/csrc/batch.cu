@@ -14,6 +14,7 @@
 #include "batch.h"
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace glmsur {
 
@@ -32,12 +33,19 @@ struct Smem {
   int* r_loc;      // G
   double* red;     // (kBT / 32) * K
   double* colv;    // 4 * K
-  double* tile64;  // kTR x G x K
+  double* tile64;  // kTR x G x K           (float64 passes; shares space with ibuf)
   float* tile32;   // 2 x kTR x G x K
+  float* ibuf;     // inner passes: 2 stages of [u | g | w | Q] row tiles
   double* e64;     // np x K
   float* e32;      // np x K
-  void* qtile;     // kTR x np rows of Q (float64 or float32), staged per row tile
+  void* qtile;     // kTR x np rows of Q (float64), staged per row tile (shares space with ibuf)
+  int maxG, maxNp; // the batch's largest G and n' (the carve's dimensions)
 };
+
+// Floats of one inner-pipeline stage: u, g, w tiles (kTR x G x K) and Q rows (kTR x np).
+__host__ __device__ inline size_t stage_floats(int K, int kTR, int maxG, int maxNp) {
+  return (size_t)3 * kTR * maxG * K + (size_t)kTR * maxNp;
+}
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -47,9 +55,11 @@ __host__ __device__ inline size_t smem_bytes(int K, int kTR, int maxG, int maxNp
   b += align16(sizeof(float) * maxG * ((maxG + 3) & ~3));
   b += align16(sizeof(int) * maxG) * 2 + align16(sizeof(int) * (maxG + 1));
   b += align16(sizeof(double) * (kBT / 32) * K) + align16(sizeof(double) * 4 * K);
-  b += align16(sizeof(double) * kTR * maxG * K) + align16(sizeof(float) * 2 * kTR * maxG * K);
+  b += align16(sizeof(float) * 2 * kTR * maxG * K);
   b += align16(sizeof(double) * maxNp * K) + align16(sizeof(float) * maxNp * K);
-  b += align16(sizeof(double) * kTR * maxNp);
+  const size_t f64 = align16(sizeof(double) * kTR * maxG * K) + align16(sizeof(double) * kTR * maxNp);
+  const size_t pipe = sizeof(float) * 2 * stage_floats(K, kTR, maxG, maxNp);
+  b += f64 > pipe ? f64 : pipe;
   return b;
 }
 
@@ -64,11 +74,14 @@ __device__ inline Smem carve(unsigned char* base, int K, int kTR, int maxG, int 
   s.poff = reinterpret_cast<int*>(base + o); o += align16(sizeof(int) * (maxG + 1));
   s.red = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (kBT / 32) * K);
   s.colv = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * 4 * K);
-  s.tile64 = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * kTR * maxG * K);
   s.tile32 = reinterpret_cast<float*>(base + o); o += align16(sizeof(float) * 2 * kTR * maxG * K);
   s.e64 = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * maxNp * K);
   s.e32 = reinterpret_cast<float*>(base + o); o += align16(sizeof(float) * maxNp * K);
-  s.qtile = base + o;
+  s.tile64 = reinterpret_cast<double*>(base + o);
+  s.qtile = base + o + align16(sizeof(double) * kTR * maxG * K);
+  s.ibuf = reinterpret_cast<float*>(base + o);
+  s.maxG = maxG;
+  s.maxNp = maxNp;
   return s;
 }
 
@@ -89,6 +102,28 @@ __device__ void cta_sum_strided(double v, double* red, double* out) {
     out[threadIdx.x] = t;
   }
   __syncthreads();
+}
+
+// Ampere-style asynchronous 16-byte copies global -> shared (no registers
+// held while in flight), grouped and awaited with wait_group.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Start copying n floats src -> dst (both 16-byte aligned, n a multiple of 4
+// when vec4): asynchronously in 16-byte pieces, else as plain copies that are
+// complete on return.
+__device__ __forceinline__ void copy_async(const float* src, float* dst, int n, bool vec4) {
+  if (vec4) {
+    for (int e = 4 * threadIdx.x; e < n; e += 4 * kBT) cp_async16(dst + e, src + e);
+  } else {
+    for (int e = threadIdx.x; e < n; e += kBT) dst[e] = __ldcg(src + e);
+  }
 }
 
 // dst[0..n) = src[0..n) (float32 row tile of a (M, G, K) vector; all
@@ -146,6 +181,54 @@ __device__ __forceinline__ void sigma_rows(const T* __restrict__ U, int tr, int 
     for (int a = 0; a < 4; ++a) {
       const int e = e0 + a * kBT;
       if (e < n) epi(e, ub[a] / (G * K), hh[a], ub[a] % K, sv[a]);
+    }
+  }
+}
+
+// float32 form of sigma_rows: a thread item is (row r, column quad hq,
+// right-hand side j), j fastest so that a thread keeps one j (kBT is a
+// multiple of K); S[r, 4hq..4hq+3, j] = sum_g U[r, g, j] Omega[g, 4hq..]
+// takes one shared load of U and one float4 (broadcast) load of an Omega row
+// per four FMAs.  Two items per thread in flight.  Calls epi(e, r, h, j, S)
+// for every h < G of the item.
+template <int K, typename Epi>
+__device__ __forceinline__ void sigma_rows4(const float* __restrict__ U, int tr, int G, int Gq,
+                                            const float* __restrict__ om, Epi epi) {
+  const int nhq = Gq >> 2;
+  const int n = tr * nhq * K;
+  const int j = threadIdx.x % K;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 2 * kBT) {
+    int rr[2], h0[2];
+    float sv[2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int item = i0 + a * kBT < n ? i0 + a * kBT : i0;
+      const int rest = item / K;
+      rr[a] = rest / nhq;
+      h0[a] = 4 * (rest - rr[a] * nhq);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sv[a][c] = 0.f;
+    }
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const float u = U[(rr[a] * G + g) * K + j];
+        const float4 o = *reinterpret_cast<const float4*>(om + g * Gq + h0[a]);
+        sv[a][0] += u * o.x;
+        sv[a][1] += u * o.y;
+        sv[a][2] += u * o.z;
+        sv[a][3] += u * o.w;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      if (i0 + a * kBT < n) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int h = h0[a] + c;
+          if (h < G) epi((rr[a] * G + h) * K + j, rr[a], h, j, sv[a][c]);
+        }
+      }
     }
   }
 }
@@ -246,7 +329,9 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
   double* e64 = sm.e64;
   float* e32 = sm.e32;
   double* qt64 = reinterpret_cast<double*>(sm.qtile);
-  float* qt32 = reinterpret_cast<float*>(sm.qtile);
+  // 16-byte asynchronous copies need 16-byte aligned row tiles: G K a
+  // multiple of 4 and a 16-byte aligned instance offset in the vector pools
+  const bool vec_ok = ((dsc.G * K) % 4 == 0) && (dsc.v_off % 4 == 0);
   const int G = dsc.G, Gq = dsc.Gq;
   const int64_t M = dsc.M, GK = (int64_t)G * K;
   const int64_t nv = M * GK;
@@ -374,30 +459,54 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
       // pass A: u = g + mu u ; S = U Omega ; d = u.S ; e = Q^T S
       float acc32[kPairsPerThread][4] = {};
       double dd = 0.0;
-      for (int64_t t0 = 0; t0 < M; t0 += kTR) {
+      const int ntiles = (int)((M + kTR - 1) / kTR);
+      const size_t sf = stage_floats(K, kTR, sm.maxG, sm.maxNp);
+      // stage layout: u | g | w | Q (tile strides of the largest instance)
+      auto stage = [&](int b) { return sm.ibuf + b * sf; };
+      const int tstride = kTR * sm.maxG * K;
+      auto issue = [&](int t, bool with_w) {
+        const int64_t t0 = (int64_t)t * kTR;
         const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
-        float* gt = reinterpret_cast<float*>(tile64);   // g tile (tile64 is free in the inner solve)
-        copy_tile<K>(u32 + t0 * GK, tile32, tr * (int)GK);
-        copy_tile<K>(g32 + t0 * GK, gt, tr * (int)GK);
-        I.stage_q(P.q32, t0, tr, qt32);
+        float* st = stage(t & 1);
+        copy_async(u32 + t0 * GK, st, tr * (int)GK, vec_ok);
+        copy_async(g32 + t0 * GK, st + tstride, tr * (int)GK, vec_ok);
+        if (with_w) copy_async(w32 + t0 * GK, st + 2 * tstride, tr * (int)GK, vec_ok);
+        copy_async(P.q32 + dsc.q_off + t0 * dsc.np, st + 3 * tstride, tr * dsc.np, true);
+        cp_async_commit();
+      };
+      issue(0, false);
+      for (int t = 0; t < ntiles; ++t) {
+        const int64_t t0 = (int64_t)t * kTR;
+        const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
+        if (t + 1 < ntiles) {
+          issue(t + 1, false);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
         __syncthreads();
+        float* ut = stage(t & 1);
+        const float* gt = ut + tstride;
+        const float* qt = ut + 3 * tstride;
         for (int e = tid; e < tr * GK; e += kBT) {
           const int j = e % K;
           if (s_act[j]) {
-            const float un = gt[e] + (float)s_mu[j] * tile32[e];
-            tile32[e] = un;     // u tile
+            const float un = gt[e] + (float)s_mu[j] * ut[e];
+            ut[e] = un;
             u32[t0 * GK + e] = un;
           }
         }
         __syncthreads();
-        // S tile into the second half of tile32, d partials
-        float* St = tile32 + kTR * GK;
-        sigma_rows<K>(tile32, tr, G, Gq, sm.om32, [&](int e, int, int, int, float sv) {
+        // S tile into tile32, d partials
+        float* St = tile32;
+        float ddt = 0.f;
+        sigma_rows4<K>(ut, tr, G, Gq, sm.om32, [&](int e, int, int, int, float sv) {
           St[e] = sv;
-          dd += (double)(sv * tile32[e]);
+          ddt += sv * ut[e];
         });
+        dd += (double)ddt;
         __syncthreads();
-        I.accumulate(qt32, St, tr, acc32);
+        I.accumulate(qt, St, tr, acc32);
         __syncthreads();
       }
       I.store_acc(acc32, e32);
@@ -413,26 +522,34 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
       __syncthreads();
       // pass B: t = S - Q e ; g -= lam t ; w -= lam u ; c' = g.g
       double cn = 0.0;
-      for (int64_t t0 = 0; t0 < M; t0 += kTR) {
+      issue(0, true);
+      for (int t = 0; t < ntiles; ++t) {
+        const int64_t t0 = (int64_t)t * kTR;
         const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
-        float* gt = tile32 + kTR * GK;                  // g tile
-        float* wt = reinterpret_cast<float*>(tile64);   // w tile
-        copy_tile<K>(u32 + t0 * GK, tile32, tr * (int)GK);
-        copy_tile<K>(g32 + t0 * GK, gt, tr * (int)GK);
-        copy_tile<K>(w32 + t0 * GK, wt, tr * (int)GK);
-        I.stage_q(P.q32, t0, tr, qt32);
+        if (t + 1 < ntiles) {
+          issue(t + 1, true);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
         __syncthreads();
-        sigma_rows<K>(tile32, tr, G, Gq, sm.om32, [&](int e, int r, int h, int j, float sv) {
+        const float* ut = stage(t & 1);
+        const float* gt = ut + tstride;
+        const float* wt = ut + 2 * tstride;
+        const float* qt = ut + 3 * tstride;
+        float cnt = 0.f;
+        sigma_rows4<K>(ut, tr, G, Gq, sm.om32, [&](int e, int r, int h, int j, float sv) {
           const int64_t gi = t0 * GK + e;
           const float lj = (float)s_lam[j];
-          const float tval = sv - I.qe_tile(qt32, e32, r, h, j);
+          const float tval = sv - I.qe_tile(qt, e32, r, h, j);
           const float gn = gt[e] - lj * tval;
           g32[gi] = gn;
           const float wo = wt[e];
           if (s_snap[j]) wb32[gi] = wo;   // the w whose c was a new quarter-low
-          w32[gi] = wo - lj * tile32[e];
-          cn += (double)(gn * gn);
+          w32[gi] = wo - lj * ut[e];
+          cnt += gn * gn;
         });
+        cn += (double)cnt;
         __syncthreads();
       }
       cta_sum_strided<K>(cn, sm.red, sm.colv + 3 * K);
@@ -537,7 +654,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
 }
 
 template <int K, int kTR>
-__global__ void __launch_bounds__(kBT)
+__global__ void __launch_bounds__(kBT, 2)
 k_batch_solve(const BatchInst* __restrict__ insts, int count, BatchPools P, BatchOpts o, int* counter, int maxG,
               int maxNp) {
   extern __shared__ __align__(128) unsigned char smraw[];
