@@ -296,7 +296,8 @@ glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status);
  * end.  Synchronises. */
 glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* cycles);
 /* Tile height chosen by the autotuner (0 before the first solve); tune_ms
- * (HOST, 3, nullable) receives the timed candidates (8, 16, 32 rows). */
+ * (HOST, 3, nullable) receives the timed candidates (8, 16, 32 rows; 0 = not
+ * timed: tuning stops once a candidate is 10% slower than the best). */
 int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms);
 int64_t glm_sur_batch_launch_count(glm_sur_batch_t h);
 void glm_sur_batch_destroy(glm_sur_batch_t h);

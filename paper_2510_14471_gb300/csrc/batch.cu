@@ -20,7 +20,7 @@ namespace glmsur {
 
 namespace {
 
-constexpr int kBT = 256;          // threads per CTA
+constexpr int kBT = 512;          // threads per CTA (one CTA per SM: 16 warps)
 constexpr int kPairsPerThread = 4;
 
 // Shared memory of one CTA (carved from dynamic shared memory; sizes follow
@@ -285,13 +285,31 @@ struct Inst {
     }
   }
 
-  // (Q e)[row r of the staged tile, i, j] = sum over block i's columns
-  template <typename TQ, typename TE>
-  __device__ TE qe_tile(const TQ* Qt, const TE* e, int r, int i, int j) const {
-    const TQ* qp = Qt + r * d.np + sm.poff[i];
-    const TE* ep = e + sm.poff[i] * K + j;
-    TE s = 0;
-    for (int c = 0; c < sm.n_i[i]; ++c) s += (TE)qp[c] * ep[c * K];
+  // Write the float32 accumulators transposed, eT[j * np + col], so that one
+  // right-hand side's coefficients are contiguous (float4 reads in qe_tile).
+  __device__ void store_acc_t(float (&acc)[kPairsPerThread][4], float* eT) const {
+    const int npairs = d.nq * K;
+#pragma unroll
+    for (int a = 0; a < kPairsPerThread; ++a) {
+      const int pr = threadIdx.x + a * kBT;
+      if (pr < npairs) {
+        const int q = pr / K, j = pr % K;
+        *reinterpret_cast<float4*>(eT + j * d.np + 4 * q) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+      }
+    }
+  }
+
+  // (Q e)[row r of the staged tile, i, j] = sum over block i's (padded) columns,
+  // four at a time (the pad columns of Q are zero)
+  __device__ float qe_tile(const float* Qt, const float* eT, int r, int i, int j) const {
+    const int c0 = sm.poff[i], nq_i = (sm.poff[i + 1] - c0) >> 2;
+    const float4* qp = reinterpret_cast<const float4*>(Qt + r * d.np + c0);
+    const float4* ep = reinterpret_cast<const float4*>(eT + j * d.np + c0);
+    float s = 0.f;
+    for (int q = 0; q < nq_i; ++q) {
+      const float4 a = qp[q], b = ep[q];
+      s += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
     return s;
   }
 
@@ -431,6 +449,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
     // Per-column state of the inner solve.  It is the same for every thread,
     // so it lives in shared memory, written by thread j < K between barriers.
     __shared__ double s_c1[K], s_c[K], s_cbest[K], s_csnap[K], s_cstop[K], s_mu[K], s_lam[K];
+    __shared__ float s_mu32[K], s_lam32[K];   // float copies read per element (no conversions there)
     __shared__ int s_ibest[K], s_act[K], s_done[K], s_snap[K], s_conv[K];
     {
       double cs = 0.0;
@@ -447,6 +466,8 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
         s_conv[tid] = 0;
         s_mu[tid] = 0.0;
         s_lam[tid] = 0.0;
+        s_mu32[tid] = 0.f;
+        s_lam32[tid] = 0.f;
       }
       __syncthreads();
     }
@@ -491,7 +512,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
         for (int e = tid; e < tr * GK; e += kBT) {
           const int j = e % K;
           if (s_act[j]) {
-            const float un = gt[e] + (float)s_mu[j] * ut[e];
+            const float un = gt[e] + s_mu32[j] * ut[e];
             ut[e] = un;
             u32[t0 * GK + e] = un;
           }
@@ -509,7 +530,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
         I.accumulate(qt, St, tr, acc32);
         __syncthreads();
       }
-      I.store_acc(acc32, e32);
+      I.store_acc_t(acc32, e32);
       cta_sum_strided<K>(dd, sm.red, sm.colv + 2 * K);
       if (tid < K) {
         const double dj = sm.colv[2 * K + tid];
@@ -518,6 +539,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
           if (!(dj > 0.0) || !isfinite(dj)) s_act[tid] = 0;
           else s_lam[tid] = s_c[tid] / dj;
         }
+        s_lam32[tid] = (float)s_lam[tid];
       }
       __syncthreads();
       // pass B: t = S - Q e ; g -= lam t ; w -= lam u ; c' = g.g
@@ -540,7 +562,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
         float cnt = 0.f;
         sigma_rows4<K>(ut, tr, G, Gq, sm.om32, [&](int e, int r, int h, int j, float sv) {
           const int64_t gi = t0 * GK + e;
-          const float lj = (float)s_lam[j];
+          const float lj = s_lam32[j];
           const float tval = sv - I.qe_tile(qt, e32, r, h, j);
           const float gn = gt[e] - lj * tval;
           g32[gi] = gn;
@@ -574,6 +596,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
             s_c[j] = cj;
           }
         }
+        s_mu32[j] = (float)s_mu[j];
       }
       __syncthreads();
     }
@@ -654,7 +677,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
 }
 
 template <int K, int kTR>
-__global__ void __launch_bounds__(kBT, 2)
+__global__ void __launch_bounds__(kBT, 1)
 k_batch_solve(const BatchInst* __restrict__ insts, int count, BatchPools P, BatchOpts o, int* counter, int maxG,
               int maxNp) {
   extern __shared__ __align__(128) unsigned char smraw[];

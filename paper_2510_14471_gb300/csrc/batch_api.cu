@@ -85,6 +85,32 @@ __global__ void k_pad_omegas(int count, const int* __restrict__ G, const int64_t
 
 }  // namespace
 
+// Descriptors of every instance in work order: decreasing `cost` (longest
+// processing time first, so that the persistent CTAs finish together).
+static cudaError_t write_work_order(glm_sur_batch_ctx* h, int k, const std::vector<double>& cost) {
+  std::vector<int> order(h->count);
+  for (int j = 0; j < h->count; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<int64_t> voff(h->count), yoff(h->count), boff(h->count);
+  int64_t v = 0, y = 0, bo = 0;
+  for (int j = 0; j < h->count; ++j) {
+    voff[j] = v; yoff[j] = y; boff[j] = bo;
+    v += (int64_t)h->M[j] * h->G[j] * k;
+    y += (int64_t)h->M[j] * h->G[j] * k;
+    bo += (int64_t)h->n[j] * k;
+  }
+  std::vector<BatchInst> insts(h->count);
+  for (int r = 0; r < h->count; ++r) {
+    const int j = order[r];
+    BatchInst& d = insts[r];
+    d.index = j;
+    d.G = h->G[j]; d.Gq = round_up4(h->G[j]); d.M = h->M[j]; d.n = h->n[j]; d.np = h->np[j]; d.nq = h->nq[j];
+    d.blk0 = h->blk0[j]; d.quad0 = h->quad0[j];
+    d.q_off = h->q_off[j]; d.om_off = h->om_off[j]; d.v_off = voff[j]; d.y_off = yoff[j]; d.b_off = boff[j];
+  }
+  return cudaMemcpy(h->d_insts, insts.data(), sizeof(BatchInst) * h->count, cudaMemcpyHostToDevice);
+}
+
 extern "C" {
 
 glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G, const int* M, const int* n_i,
@@ -224,33 +250,11 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     h->kcap = k;
   }
   if (h->insts_k != k) {
-    // work order: most expensive instances first (cost ~ M * (G^2 + 2 n')), so
-    // the persistent CTAs finish together
-    std::vector<int> order(h->count);
-    for (int j = 0; j < h->count; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-      const double ca = (double)h->M[a] * (h->G[a] * h->G[a] + 2.0 * h->np[a]);
-      const double cc = (double)h->M[c] * (h->G[c] * h->G[c] + 2.0 * h->np[c]);
-      return ca > cc;
-    });
-    std::vector<int64_t> voff(h->count), yoff(h->count), boff(h->count);
-    int64_t v = 0, y = 0, bo = 0;
-    for (int j = 0; j < h->count; ++j) {
-      voff[j] = v; yoff[j] = y; boff[j] = bo;
-      v += (int64_t)h->M[j] * h->G[j] * k;
-      y += (int64_t)h->M[j] * h->G[j] * k;
-      bo += (int64_t)h->n[j] * k;
-    }
-    std::vector<BatchInst> insts(h->count);
-    for (int r = 0; r < h->count; ++r) {
-      const int j = order[r];
-      BatchInst& d = insts[r];
-      d.index = j;
-      d.G = h->G[j]; d.Gq = round_up4(h->G[j]); d.M = h->M[j]; d.n = h->n[j]; d.np = h->np[j]; d.nq = h->nq[j];
-      d.blk0 = h->blk0[j]; d.quad0 = h->quad0[j];
-      d.q_off = h->q_off[j]; d.om_off = h->om_off[j]; d.v_off = voff[j]; d.y_off = yoff[j]; d.b_off = boff[j];
-    }
-    GS_CUDA_TRY(cudaMemcpy(h->d_insts, insts.data(), sizeof(BatchInst) * h->count, cudaMemcpyHostToDevice));
+    // first work order: most expensive steps first (cost ~ M (G^2 + 2 n'));
+    // replaced by the measured times once the autotuner has run the batch
+    std::vector<double> cost(h->count);
+    for (int j = 0; j < h->count; ++j) cost[j] = (double)h->M[j] * (h->G[j] * h->G[j] + 2.0 * h->np[j]);
+    GS_CUDA_TRY(write_work_order(h, k, cost));
     h->insts_k = k;
     h->tile = 0;
     if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -261,12 +265,13 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
                h->relres_d, h->steps_d, h->cycles_d};
   BatchOpts bo{h->opts.tol, h->opts.inner_tol, h->opts.max_refine, 4000, 25};
   if (h->tile == 0) {
-    // autotune: time one batch solve per tile height, keep the fastest
+    // autotune: time one batch solve per tile height, tallest first, keep the
+    // fastest; stop once a candidate is 10% slower than the best so far
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 2; t >= 0; --t) {
       const int TR = kBatchTiles[t];
       int ctas = 0;
       if (batch_prepare(k, TR, h->maxG, h->maxNp, &ctas) != cudaSuccess) {
@@ -284,10 +289,16 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
       h->tune_ms[t] = ms;
       h->launches += 2;
       if (ms < best) { best = ms; h->tile = TR; h->grid = grid; }
+      else if (ms > 1.1f * best) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (h->tile == 0) return GLM_SUR_INVALID_ARG;
+    // re-order by the measured time of every instance in the last tuning run
+    std::vector<long long> cyc(h->count);
+    GS_CUDA_TRY(cudaMemcpy(cyc.data(), h->cycles_d, sizeof(long long) * h->count, cudaMemcpyDeviceToHost));
+    std::vector<double> cost(cyc.begin(), cyc.end());
+    GS_CUDA_TRY(write_work_order(h, k, cost));
   }
   // one persistent launch, replayed from a captured graph while the buffers stay the same
   const void* key[5] = {Y, b, iters, relres, nullptr};

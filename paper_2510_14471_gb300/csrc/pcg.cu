@@ -123,6 +123,28 @@ __device__ double reduce_cols_strided(double v, double* red) {
   return s;
 }
 
+// Same reduction when every thread holds four columns, 4 (tid % (JJ/4)) + c
+// (c = 0..3).  Valid in threads tid < JJ.
+template <int JJ>
+__device__ double reduce_cols_quads(const double (&v)[4], double* red) {
+  constexpr int JQ = JJ / 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x[4] = {v[0], v[1], v[2], v[3]};
+#pragma unroll
+  for (int off = 16; off >= JQ; off >>= 1)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] += __shfl_xor_sync(0xffffffffu, x[c], off);
+  __syncthreads();
+  if (lane < JQ)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[warp * JJ + 4 * lane + c] = x[c];
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < JJ)
+    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
+  return s;
+}
+
 // out[jj] = sum_{p < np} part[p*k + j0 + jj] for jj < JJ, using the whole CTA
 // (fixed order: deterministic).  Valid in threads tid < JJ.
 template <int JJ>
@@ -826,6 +848,11 @@ k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict
   if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
 }
 
+// float32 with whole quads of right-hand sides: the TMA sigma step works on
+// float4 (four right-hand sides) per thread
+template <typename T, int JJ>
+constexpr bool kQuadSigma = sizeof(T) == 4 && JJ % 4 == 0 && JJ >= 4;
+
 template <typename T, int JJ, int RI>
 __global__ void __launch_bounds__(512, 1)
 k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict__ Om, const T* __restrict__ g,
@@ -838,7 +865,7 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
   const int64_t GK = (int64_t)G * JJ;
   const int64_t stage_elems = (int64_t)TR * 3 * GK;
   __shared__ double red[16 * 16];
-  __shared__ double mu_s[JJ], lamp_s[JJ];
+  __shared__ T mu_s[JJ], lamp_s[JJ];   // in the working precision: no conversion per element
   __shared__ int act_s[JJ], snap_s[JJ], anyp_s, abort_s;
   const int tid = threadIdx.x;
   if (*st.err) return;   // an earlier bounded wait gave up: the run is being abandoned
@@ -846,8 +873,8 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
   const double csum = sum_partials<JJ>(cpart, ncpart, JJ, 0, red);
   if (tid < JJ) {
     const StepScalars sc = step_prologue(st, tid, JJ, csum, blockIdx.x == 0);
-    mu_s[tid] = sc.mu;
-    lamp_s[tid] = sc.lam_prev;
+    mu_s[tid] = (T)sc.mu;
+    lamp_s[tid] = (T)sc.lam_prev;
     act_s[tid] = sc.act;
     snap_s[tid] = sc.snap;
     if (sc.act_prev) atomicOr(&anyp_s, 1);
@@ -881,6 +908,7 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
   const int nhq = Gq >> 2;
   const int jj_t = tid % JJ;
   double dsum = 0.0;
+  double dsq[4] = {0.0, 0.0, 0.0, 0.0};   // quad path: columns 4 (tid % (JJ/4)) + c
   for (int tile = 0; tile < ntiles; ++tile) {
     const int sidx = tile % NST;
     if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
@@ -899,20 +927,163 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
     const T* ws = gs + (int64_t)2 * TR * GK;
     // elementwise (contiguous tile): w -= lam_prev u_old ; u = g + mu u_old
     const int ne = tr * (int)GK;
-    for (int e = tid; e < ne; e += blockDim.x) {
-      const int jj = e % JJ;
-      const T uo = us[e];
-      const T lp = (T)lamp_s[jj];
-      const T wn = ws[e] - lp * uo;
-      if (lp != (T)0) w[row0 * GK + e] = wn;
-      if (snap_s[jj]) wbest[row0 * GK + e] = wn;
-      if (act_s[jj]) {
-        const T un = gs[e] + (T)mu_s[jj] * uo;
-        u[row0 * GK + e] = un;
-        us[e] = un;
+    if constexpr (kQuadSigma<T, JJ>) {
+      // four consecutive right-hand sides per thread (float4 in shared and global memory)
+      for (int e4 = tid; e4 < (ne >> 2); e4 += blockDim.x) {
+        const int jj0 = (4 * e4) % JJ;
+        float4 uo = reinterpret_cast<const float4*>(us)[e4];
+        const float4 wo = reinterpret_cast<const float4*>(ws)[e4];
+        const float4 go = reinterpret_cast<const float4*>(gs)[e4];
+        const float4 lp = make_float4(lamp_s[jj0], lamp_s[jj0 + 1], lamp_s[jj0 + 2], lamp_s[jj0 + 3]);
+        const float4 wn = make_float4(wo.x - lp.x * uo.x, wo.y - lp.y * uo.y, wo.z - lp.z * uo.z, wo.w - lp.w * uo.w);
+        float4* wg = reinterpret_cast<float4*>(w + row0 * GK) + e4;
+        if (lp.x != 0.f || lp.y != 0.f || lp.z != 0.f || lp.w != 0.f) *wg = wn;   // unchanged lanes rewrite w
+        const int sn = snap_s[jj0] + snap_s[jj0 + 1] + snap_s[jj0 + 2] + snap_s[jj0 + 3];
+        if (sn == 4) {
+          reinterpret_cast<float4*>(wbest + row0 * GK)[e4] = wn;
+        } else if (sn) {
+          float* wb = wbest + row0 * GK + 4 * e4;
+          if (snap_s[jj0]) wb[0] = wn.x;
+          if (snap_s[jj0 + 1]) wb[1] = wn.y;
+          if (snap_s[jj0 + 2]) wb[2] = wn.z;
+          if (snap_s[jj0 + 3]) wb[3] = wn.w;
+        }
+        const int na = act_s[jj0] + act_s[jj0 + 1] + act_s[jj0 + 2] + act_s[jj0 + 3];
+        if (na) {
+          if (act_s[jj0]) uo.x = go.x + mu_s[jj0] * uo.x;
+          if (act_s[jj0 + 1]) uo.y = go.y + mu_s[jj0 + 1] * uo.y;
+          if (act_s[jj0 + 2]) uo.z = go.z + mu_s[jj0 + 2] * uo.z;
+          if (act_s[jj0 + 3]) uo.w = go.w + mu_s[jj0 + 3] * uo.w;
+          reinterpret_cast<float4*>(u + row0 * GK)[e4] = uo;   // inactive lanes rewrite their u
+          reinterpret_cast<float4*>(us)[e4] = uo;
+        }
+      }
+    } else {
+      for (int e = tid; e < ne; e += blockDim.x) {
+        const int jj = e % JJ;
+        const T uo = us[e];
+        const T lp = lamp_s[jj];
+        const T wn = ws[e] - lp * uo;
+        if (lp != (T)0) w[row0 * GK + e] = wn;
+        if (snap_s[jj]) wbest[row0 * GK + e] = wn;
+        if (act_s[jj]) {
+          const T un = gs[e] + mu_s[jj] * uo;
+          u[row0 * GK + e] = un;
+          us[e] = un;
+        }
       }
     }
     __syncthreads();
+    if constexpr (kQuadSigma<T, JJ>) {
+      // S = U Omega: item = (row pair, h quad, jj quad); per g one float4 of U
+      // per row and one float4 of Omega give 32 FMAs
+      constexpr int JQ = JJ / 4, RR = 2;
+      const int ngrp = (tr + RR - 1) / RR;
+      const int nitems = ngrp * nhq * JQ;
+      const int jq = tid % JQ;   // fixed per thread: blockDim is a multiple of JQ
+      float dq[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int itm = tid; itm < nitems; itm += blockDim.x) {
+        const int rest = itm / JQ;
+        const int hq = rest % nhq, tg = rest / nhq;
+        const float* ur[RR];
+#pragma unroll
+        for (int a = 0; a < RR; ++a) {
+          const int t = RR * tg + a;
+          ur[a] = us + (int64_t)(t < tr ? t : RR * tg) * GK + 4 * jq;
+        }
+        float4 acc[RR][4];
+#pragma unroll
+        for (int a = 0; a < RR; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int gg = 0; gg < G; ++gg) {
+          const float4 om = *reinterpret_cast<const float4*>(Om_s + (int64_t)gg * Gq + 4 * hq);
+#pragma unroll
+          for (int a = 0; a < RR; ++a) {
+            const float4 v = *reinterpret_cast<const float4*>(ur[a] + gg * JJ);
+            const float oc[4] = {om.x, om.y, om.z, om.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              acc[a][c].x += v.x * oc[c];
+              acc[a][c].y += v.y * oc[c];
+              acc[a][c].z += v.z * oc[c];
+              acc[a][c].w += v.w * oc[c];
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < RR; ++a) {
+          const int t = RR * tg + a;
+          if (t < tr) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int h = 4 * hq + c;
+              if (h < G) {
+                *reinterpret_cast<float4*>(S + (row0 + t) * GK + h * JJ + 4 * jq) = acc[a][c];
+                const float4 uh = *reinterpret_cast<const float4*>(ur[a] + h * JJ);
+                dq[0] += acc[a][c].x * uh.x;
+                dq[1] += acc[a][c].y * uh.y;
+                dq[2] += acc[a][c].z * uh.z;
+                dq[3] += acc[a][c].w * uh.w;
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dsq[c] += (double)dq[c];
+    } else if (sizeof(T) == 4 && JJ == 1 && (G & 3) == 0) {
+      // one right-hand side, G a multiple of 4: item = (4 rows, h quad); per
+      // four g one float4 of U per row and four float4 Omega rows give 64 FMAs
+      constexpr int RR = 4;
+      const int ngrp = (tr + RR - 1) / RR;
+      const int nitems = ngrp * nhq;
+      float dl = 0.f;
+      for (int itm = tid; itm < nitems; itm += blockDim.x) {
+        const int hq = itm % nhq, tg = itm / nhq;
+        const float* ur[RR];
+#pragma unroll
+        for (int a = 0; a < RR; ++a) {
+          const int t = RR * tg + a;
+          ur[a] = reinterpret_cast<const float*>(us) + (int64_t)(t < tr ? t : RR * tg) * G;
+        }
+        float acc[RR][4];
+#pragma unroll
+        for (int a = 0; a < RR; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+        for (int g0 = 0; g0 < G; g0 += 4) {
+          float4 uv[RR];
+#pragma unroll
+          for (int a = 0; a < RR; ++a) uv[a] = *reinterpret_cast<const float4*>(ur[a] + g0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 om = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Om_s) +
+                                                               (int64_t)(g0 + q) * Gq + 4 * hq);
+#pragma unroll
+            for (int a = 0; a < RR; ++a) {
+              const float x = q == 0 ? uv[a].x : q == 1 ? uv[a].y : q == 2 ? uv[a].z : uv[a].w;
+              acc[a][0] += x * om.x;
+              acc[a][1] += x * om.y;
+              acc[a][2] += x * om.z;
+              acc[a][3] += x * om.w;
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < RR; ++a) {
+          const int t = RR * tg + a;
+          if (t < tr) {
+            // h quad lies inside the row: G is a multiple of 4
+            *reinterpret_cast<float4*>(reinterpret_cast<float*>(S) + (row0 + t) * GK + 4 * hq) =
+                make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+            const float4 uh = *reinterpret_cast<const float4*>(ur[a] + 4 * hq);
+            dl += acc[a][0] * uh.x + acc[a][1] * uh.y + acc[a][2] * uh.z + acc[a][3] * uh.w;
+          }
+        }
+      }
+      dsum += (double)dl;
+    } else {
     // S = U Omega: item = (RI-row group, h quad, jj), RI x 4 outputs per item
     const int ngrp = (tr + RI - 1) / RI;
     const int nitems = ngrp * nhq * JJ;
@@ -957,10 +1128,13 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
       }
     }
     dsum += (double)dloc;
+    }
     __syncthreads();
     if (tid == 0 && issued < ntiles) issue(issued++);
   }
-  const double d = reduce_cols_strided<JJ>(dsum, red);
+  double d;
+  if constexpr (kQuadSigma<T, JJ>) d = reduce_cols_quads<JJ>(dsq, red);
+  else d = reduce_cols_strided<JJ>(dsum, red);
   if (tid < JJ) dpart[(int64_t)blockIdx.x * JJ + tid] = d;
 }
 
