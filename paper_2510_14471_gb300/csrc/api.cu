@@ -214,6 +214,20 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
         p.tma_update = true;   // same grid and partial layout
       }
     }
+    // projection partials: a thread per column quad, rows of Q and S streamed
+    if (gm.nq <= 512) {
+      const size_t row_stage = sz * (size_t)gm.np + GK_bytes;
+      p.nst_partial = 3;
+      const size_t trp = (budget_tma - 128) / (p.nst_partial * row_stage);
+      if (trp >= 1) {
+        p.tr_partial = (int)std::min<size_t>(16, trp);
+        p.partial_tma_smem = 128 + (size_t)p.nst_partial * p.tr_partial * row_stage;
+        p.partial_threads = (int)std::max<int64_t>(64, ceil_div(gm.nq, 32) * 32);
+        p.tma_partial = true;
+        p.n_partial_rows = h->sms;
+        p.n_qgroups = 1;
+      }
+    }
     if (p.tma_sigma) p.n_sigma = h->sms;
     if (p.tma_update) {
       p.n_update = h->sms;
@@ -223,13 +237,15 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   }
   cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem, p.update_smem)
                             : set_smem_attrs<float>(p.JJ, p.sigma_smem, p.update_smem);
-  if (e == cudaSuccess && (p.tma_sigma || p.tma_update))
+  if (e == cudaSuccess && (p.tma_sigma || p.tma_update || p.tma_partial))
     e = is_double ? set_tma_smem_attrs<double>(p.JJ, std::max<size_t>(p.sigma_tma_smem, 1024),
                                                std::max<size_t>(p.update_tma_smem, 1024),
-                                               std::max<size_t>(p.bj_smem, 1024))
+                                               std::max<size_t>(p.bj_smem, 1024),
+                                               std::max<size_t>(p.partial_tma_smem, 1024))
                   : set_tma_smem_attrs<float>(p.JJ, std::max<size_t>(p.sigma_tma_smem, 1024),
                                               std::max<size_t>(p.update_tma_smem, 1024),
-                                              std::max<size_t>(p.bj_smem, 1024));
+                                              std::max<size_t>(p.bj_smem, 1024),
+                                              std::max<size_t>(p.partial_tma_smem, 1024));
   if (e != cudaSuccess) {
     set_last_error(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
     return GLM_SUR_CUDA_ERROR;

@@ -604,6 +604,111 @@ __device__ void tma_drain(uint64_t* full, int NST, int next_tile, int issued) {
   for (int t = next_tile; t < issued; ++t) mbar_wait_bounded(&full[t % NST], (t / NST) & 1, kWaitLimitNs);
 }
 
+// proj_partial, TMA-streamed: one CTA per SM over a contiguous row range;
+// thread q owns column quad q (all JJ == k right-hand sides): per row one
+// vector of Q and JJ/4 vectors of S (the rows of its block, shared by the
+// warp) give 4 JJ FMAs.  Output layout as k_proj_partial (one partial per CTA).
+template <typename T, int JJ>
+__global__ void __launch_bounds__(512, 1)
+k_proj_partial_tma(int64_t M, int G, int np, int nq, int TR, int NST, const T* __restrict__ Q,
+                   const T* __restrict__ S, const int* __restrict__ quad_blk, T* __restrict__ Cpart, PcgState st,
+                   int use_state) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+  T* stage0 = reinterpret_cast<T*>(smraw + 128);
+  const int64_t GK = (int64_t)G * JJ;
+  const int64_t stage_elems = (int64_t)TR * (np + GK);
+  __shared__ int abort_s;
+  const int tid = threadIdx.x;
+  if (*st.err) return;   // an earlier bounded wait gave up: the run is being abandoned
+  if (use_state) {
+    const int slot = (*st.it) & 1;
+    int any = 0;
+    for (int jj = 0; jj < JJ; ++jj) any |= st.active[slot][jj];
+    if (!any) return;
+  }
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  const int ntiles = (int)((r1 - r0 + TR - 1) / TR);
+  if (tid == 0) {
+    for (int q = 0; q < NST; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int tile) {
+    const int sidx = tile % NST;
+    const int64_t row0 = r0 + (int64_t)tile * TR;
+    const int tr = (int)((r1 - row0) < TR ? (r1 - row0) : TR);
+    T* Qs = stage0 + sidx * stage_elems;
+    T* Ss = Qs + (int64_t)TR * np;
+    const uint32_t bq = (uint32_t)(tr * np * sizeof(T)), bs = (uint32_t)(tr * GK * sizeof(T));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[sidx], bq + bs);
+    tma_load_1d(Qs, Q + row0 * np, bq, &full[sidx]);
+    tma_load_1d(Ss, S + row0 * GK, bs, &full[sidx]);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < ntiles; ++issued) issue(issued);
+  const bool has = tid < nq;
+  const int blk = has ? quad_blk[tid] : 0;
+  T acc[4][JJ];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) acc[c][jj] = 0;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int sidx = tile % NST;
+    if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
+      abort_s = 1;
+      atomicExch(st.err, 1);
+    }
+    __syncthreads();
+    if (abort_s) {
+      if (tid == 0) tma_drain(full, NST, tile + 1, issued);
+      return;
+    }
+    const int64_t row0 = r0 + (int64_t)tile * TR;
+    const int tr = (int)((r1 - row0) < TR ? (r1 - row0) : TR);
+    const T* Qs = stage0 + sidx * stage_elems;
+    const T* Ss = Qs + (int64_t)TR * np;
+    if (has) {
+#pragma unroll 2
+      for (int r = 0; r < tr; ++r) {
+        T qv[4];
+        Vec4<T>::load(Qs + (int64_t)r * np + 4 * tid, qv);
+        const T* sp = Ss + (int64_t)r * GK + blk * JJ;
+        T sv[JJ];
+        if constexpr (JJ >= 4) {
+#pragma unroll
+          for (int a = 0; a < JJ / 4; ++a) {
+            T tmp[4];
+            Vec4<T>::load(sp + 4 * a, tmp);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) sv[4 * a + b] = tmp[b];
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < JJ; ++jj) sv[jj] = sp[jj];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int jj = 0; jj < JJ; ++jj) acc[c][jj] += qv[c] * sv[jj];
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && issued < ntiles) issue(issued++);
+  }
+  if (has) {
+    T* dst = Cpart + ((int64_t)blockIdx.x * np + 4 * tid) * JJ;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) dst[(int64_t)c * JJ + jj] = acc[c][jj];
+  }
+}
+
 template <typename T, int JJ>
 __global__ void __launch_bounds__(512, 1)
 k_proj_update_tma(int64_t M, int G, int np, int nq, int TRB, int NST, const T* __restrict__ Q,
@@ -1365,6 +1470,11 @@ static void launch_sigma_resid_jj(const IterPlan& p, const Geom& gm, int k, cons
 template <typename T, int JJ>
 static void launch_proj_partial_jj(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* Cpart,
                                    const PcgState& st, int use_state, cudaStream_t s) {
+  if (p.tma_partial) {
+    k_proj_partial_tma<T, JJ><<<p.n_partial_rows, p.partial_threads, p.partial_tma_smem, s>>>(
+        gm.M, gm.G, gm.np, gm.nq, p.tr_partial, p.nst_partial, Q, S, gm.d_quad_blk, Cpart, st, use_state);
+    return;
+  }
   dim3 grid(p.n_partial_rows, p.n_qgroups, k / JJ);
   const int qpg = (int)ceil_div(gm.nq, p.n_qgroups);
   const int threads = (int)std::min<int64_t>(256, ceil_div(qpg, 32) * 32);
@@ -1553,7 +1663,8 @@ template void launch_convert<double, float>(int64_t, const double*, float*, doub
 template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);
 template void launch_colsumsq<double>(const IterPlan&, const Geom&, int, const double*, double*, cudaStream_t);
 template <typename T>
-cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes) {
+cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes,
+                               size_t partial_bytes) {
   cudaError_t e = cudaSuccess;
 #define C_(J)                                                                                                      \
   e = cudaFuncSetAttribute(k_sigma_step_tma<T, J, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sigma_bytes); \
@@ -1569,13 +1680,16 @@ cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, 
   if (e == cudaSuccess)                                                                                            \
     e = cudaFuncSetAttribute(k_proj_update_bj<T, J, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bj_bytes); \
   if (e == cudaSuccess)                                                                                            \
-    e = cudaFuncSetAttribute(k_proj_update_bj<T, J, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bj_bytes);
+    e = cudaFuncSetAttribute(k_proj_update_bj<T, J, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bj_bytes); \
+  if (e == cudaSuccess)                                                                                            \
+    e = cudaFuncSetAttribute(k_proj_partial_tma<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                             (int)partial_bytes);
   GS_DISPATCH_JJ(JJ, C_)
 #undef C_
   return e;
 }
-template cudaError_t set_tma_smem_attrs<double>(int, size_t, size_t, size_t);
-template cudaError_t set_tma_smem_attrs<float>(int, size_t, size_t, size_t);
+template cudaError_t set_tma_smem_attrs<double>(int, size_t, size_t, size_t, size_t);
+template cudaError_t set_tma_smem_attrs<float>(int, size_t, size_t, size_t, size_t);
 template cudaError_t set_smem_attrs<double>(int, size_t, size_t);
 template cudaError_t set_smem_attrs<float>(int, size_t, size_t);
 

@@ -33,6 +33,9 @@ struct IterPlan {
   bool bj_update = false;  // block x column projection update (n_i <= 32, G*k <= 1024)
   int bj_np = 1, trb_bj = 1, nst_bj = 3;
   size_t bj_smem = 0;
+  bool tma_partial = false;  // TMA-streamed projection partials (n' / 4 <= 512 quads)
+  int tr_partial = 1, nst_partial = 3, partial_threads = 64;
+  size_t partial_tma_smem = 0;
 };
 
 template <typename T>
@@ -78,6 +81,7 @@ void launch_unpad_q(const Geom& gm, const double* Q, double* out, int64_t ldq, c
 template <typename T>
 cudaError_t set_smem_attrs(int JJ, size_t bytes, size_t upd_bytes);
 template <typename T>
-cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes);
+cudaError_t set_tma_smem_attrs(int JJ, size_t sigma_bytes, size_t update_bytes, size_t bj_bytes,
+                               size_t partial_bytes);
 
 }  // namespace glmsur
