@@ -467,10 +467,18 @@ k_reduce(int64_t nidx, int nrb, const T* __restrict__ Cpart, T* __restrict__ C, 
   // same launch advances it)
   const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (idx < nidx)
-    for (int r = sl; r < nrb; r += 8) s += (double)Cpart[(int64_t)r * nidx + idx];
-  part[sl][lane] = s;
+  // each slice sums its partials in the working precision (four independent
+  // chains, fixed order), the eight slices are added in float64
+  T s4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (idx < nidx) {
+    int r = sl;
+    for (; r + 24 < nrb; r += 32) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s4[a] += Cpart[(int64_t)(r + 8 * a) * nidx + idx];
+    }
+    for (int a = 0; r < nrb; r += 8, a = (a + 1) & 3) s4[a] += Cpart[(int64_t)r * nidx + idx];
+  }
+  part[sl][lane] = ((double)s4[0] + (double)s4[1]) + ((double)s4[2] + (double)s4[3]);
   __syncthreads();
   if (sl == 0 && idx < nidx) {
     double tot = 0.0;
@@ -702,10 +710,19 @@ k_proj_partial_tma(int64_t M, int G, int np, int nq, int TR, int NST, const T* _
   }
   if (has) {
     T* dst = Cpart + ((int64_t)blockIdx.x * np + 4 * tid) * JJ;
+    if constexpr (sizeof(T) == 4 && JJ % 4 == 0) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int jj = 0; jj < JJ; ++jj) dst[(int64_t)c * JJ + jj] = acc[c][jj];
+        for (int a = 0; a < JJ / 4; ++a)
+          reinterpret_cast<float4*>(dst + c * JJ)[a] =
+              make_float4(acc[c][4 * a], acc[c][4 * a + 1], acc[c][4 * a + 2], acc[c][4 * a + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int jj = 0; jj < JJ; ++jj) dst[(int64_t)c * JJ + jj] = acc[c][jj];
+    }
   }
 }
 
@@ -953,6 +970,71 @@ k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict
   if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
 }
 
+// S = U Omega on a staged row tile of float32 U (row stride GK = G JJ), items
+// (RR rows, h quad, jj quad); dq[c] accumulates d = u.S of the thread's
+// right-hand sides 4 (tid % (JJ/4)) + c in float64 per tile.
+template <int RR, int JJ>
+__device__ __forceinline__ void sigma_quads(const float* __restrict__ us, const float* __restrict__ Om_s,
+                                            float* __restrict__ S, int64_t row0, int tr, int G, int Gq, int64_t GK,
+                                            double (&dsq)[4]) {
+  constexpr int JQ = JJ / 4;
+  const int nhq = Gq >> 2;
+  const int ngrp = (tr + RR - 1) / RR;
+  const int nitems = ngrp * nhq * JQ;
+  const int jq = threadIdx.x % JQ;   // fixed per thread: blockDim is a multiple of JQ
+  float dq[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int itm = threadIdx.x; itm < nitems; itm += blockDim.x) {
+    const int rest = itm / JQ;
+    const int hq = rest % nhq, tg = rest / nhq;
+    const float* ur[RR];
+#pragma unroll
+    for (int a = 0; a < RR; ++a) {
+      const int t = RR * tg + a;
+      ur[a] = us + (int64_t)(t < tr ? t : RR * tg) * GK + 4 * jq;
+    }
+    float4 acc[RR][4];
+#pragma unroll
+    for (int a = 0; a < RR; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int gg = 0; gg < G; ++gg) {
+      const float4 om = *reinterpret_cast<const float4*>(Om_s + (int64_t)gg * Gq + 4 * hq);
+      const float oc[4] = {om.x, om.y, om.z, om.w};
+#pragma unroll
+      for (int a = 0; a < RR; ++a) {
+        const float4 v = *reinterpret_cast<const float4*>(ur[a] + gg * JJ);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[a][c].x += v.x * oc[c];
+          acc[a][c].y += v.y * oc[c];
+          acc[a][c].z += v.z * oc[c];
+          acc[a][c].w += v.w * oc[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < RR; ++a) {
+      const int t = RR * tg + a;
+      if (t < tr) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int h = 4 * hq + c;
+          if (h < G) {
+            *reinterpret_cast<float4*>(S + (row0 + t) * GK + h * JJ + 4 * jq) = acc[a][c];
+            const float4 uh = *reinterpret_cast<const float4*>(ur[a] + h * JJ);
+            dq[0] += acc[a][c].x * uh.x;
+            dq[1] += acc[a][c].y * uh.y;
+            dq[2] += acc[a][c].z * uh.z;
+            dq[3] += acc[a][c].w * uh.w;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dsq[c] += (double)dq[c];
+}
+
 // float32 with whole quads of right-hand sides: the TMA sigma step works on
 // float4 (four right-hand sides) per thread
 template <typename T, int JJ>
@@ -1080,63 +1162,16 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
     }
     __syncthreads();
     if constexpr (kQuadSigma<T, JJ>) {
-      // S = U Omega: item = (row pair, h quad, jj quad); per g one float4 of U
-      // per row and one float4 of Omega give 32 FMAs
-      constexpr int JQ = JJ / 4, RR = 2;
-      const int ngrp = (tr + RR - 1) / RR;
-      const int nitems = ngrp * nhq * JQ;
-      const int jq = tid % JQ;   // fixed per thread: blockDim is a multiple of JQ
-      float dq[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int itm = tid; itm < nitems; itm += blockDim.x) {
-        const int rest = itm / JQ;
-        const int hq = rest % nhq, tg = rest / nhq;
-        const float* ur[RR];
-#pragma unroll
-        for (int a = 0; a < RR; ++a) {
-          const int t = RR * tg + a;
-          ur[a] = us + (int64_t)(t < tr ? t : RR * tg) * GK + 4 * jq;
-        }
-        float4 acc[RR][4];
-#pragma unroll
-        for (int a = 0; a < RR; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int gg = 0; gg < G; ++gg) {
-          const float4 om = *reinterpret_cast<const float4*>(Om_s + (int64_t)gg * Gq + 4 * hq);
-#pragma unroll
-          for (int a = 0; a < RR; ++a) {
-            const float4 v = *reinterpret_cast<const float4*>(ur[a] + gg * JJ);
-            const float oc[4] = {om.x, om.y, om.z, om.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              acc[a][c].x += v.x * oc[c];
-              acc[a][c].y += v.y * oc[c];
-              acc[a][c].z += v.z * oc[c];
-              acc[a][c].w += v.w * oc[c];
-            }
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < RR; ++a) {
-          const int t = RR * tg + a;
-          if (t < tr) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int h = 4 * hq + c;
-              if (h < G) {
-                *reinterpret_cast<float4*>(S + (row0 + t) * GK + h * JJ + 4 * jq) = acc[a][c];
-                const float4 uh = *reinterpret_cast<const float4*>(ur[a] + h * JJ);
-                dq[0] += acc[a][c].x * uh.x;
-                dq[1] += acc[a][c].y * uh.y;
-                dq[2] += acc[a][c].z * uh.z;
-                dq[3] += acc[a][c].w * uh.w;
-              }
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) dsq[c] += (double)dq[c];
+      // S = U Omega: item = (RR rows, h quad, jj quad); per g one float4 of U
+      // per row and one float4 of Omega give 16 RR FMAs.  Two rows per item
+      // when the tile has enough items for every thread, else one.
+      constexpr int JQ = JJ / 4;
+      if (((tr + 1) / 2) * nhq * JQ >= (int)blockDim.x)
+        sigma_quads<2, JJ>(reinterpret_cast<const float*>(us), reinterpret_cast<const float*>(Om_s),
+                           reinterpret_cast<float*>(S), row0, tr, G, Gq, GK, dsq);
+      else
+        sigma_quads<1, JJ>(reinterpret_cast<const float*>(us), reinterpret_cast<const float*>(Om_s),
+                           reinterpret_cast<float*>(S), row0, tr, G, Gq, GK, dsq);
     } else if (sizeof(T) == 4 && JJ == 1 && (G & 3) == 0) {
       // one right-hand side, G a multiple of 4: item = (4 rows, h quad); per
       // four g one float4 of U per row and four float4 Omega rows give 64 FMAs
