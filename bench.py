@@ -162,7 +162,7 @@ def aggregate(ms_local, pg, world, device="cpu"):
     return ms, world * 1e3 / ms
 
 
-NCU_SECTION = {"sigma_step": "k_sigma_step_tma", "proj_partial": "k_proj_partial", "proj_update": "k_proj_update_bj"}
+NCU_SECTION = {"sigma_step": "k_sigma_step_tma", "proj_partial": "k_proj_partial_tma", "proj_update": "k_proj_update_bj"}
 
 
 def ncu_traffic(args, kernel):
