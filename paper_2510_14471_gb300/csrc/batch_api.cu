@@ -271,6 +271,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
+    std::vector<long long> best_cycles(h->count, 0);   // per-instance times of the fastest tile height
     for (int t = 2; t >= 0; --t) {
       const int TR = kBatchTiles[t];
       int ctas = 0;
@@ -288,16 +289,19 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
       cudaEventElapsedTime(&ms, e0, e1);
       h->tune_ms[t] = ms;
       h->launches += 2;
-      if (ms < best) { best = ms; h->tile = TR; h->grid = grid; }
-      else if (ms > 1.1f * best) break;
+      if (ms < best) {
+        best = ms; h->tile = TR; h->grid = grid;
+        GS_CUDA_TRY(cudaMemcpy(best_cycles.data(), h->cycles_d, sizeof(long long) * h->count,
+                               cudaMemcpyDeviceToHost));
+      } else if (ms > 1.1f * best) {
+        break;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (h->tile == 0) return GLM_SUR_INVALID_ARG;
-    // re-order by the measured time of every instance in the last tuning run
-    std::vector<long long> cyc(h->count);
-    GS_CUDA_TRY(cudaMemcpy(cyc.data(), h->cycles_d, sizeof(long long) * h->count, cudaMemcpyDeviceToHost));
-    std::vector<double> cost(cyc.begin(), cyc.end());
+    // re-order by the measured time of every instance at the chosen tile height
+    std::vector<double> cost(best_cycles.begin(), best_cycles.end());
     GS_CUDA_TRY(write_work_order(h, k, cost));
   }
   // one persistent launch, replayed from a captured graph while the buffers stay the same
