@@ -177,6 +177,11 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
     const int per_row_items = (gm.Gq / 4) * p.JJ;
     p.ri = per_row_items >= 256 ? 4 : (per_row_items >= 64 ? 2 : 1);
     int tr_want = p.ri * (int)ceil_div(512, per_row_items);
+    if (!is_double && p.JJ == 1 && gm.G % 4 == 0) {
+      // float4 runs of one right-hand side: two rows per item when the tile is tall enough
+      p.ri = 2;
+      tr_want = 2 * (int)ceil_div(512, gm.Gq / 4);
+    }
     tr_want = std::max(p.ri, std::min(64, tr_want));
     for (int tr = tr_want; tr >= 1 && !p.tma_sigma; tr = (tr > p.ri ? tr - p.ri : tr - 1)) {
       for (int nst = 3; nst >= 2; --nst) {

@@ -1035,6 +1035,60 @@ __device__ __forceinline__ void sigma_quads(const float* __restrict__ us, const 
   for (int c = 0; c < 4; ++c) dsq[c] += (double)dq[c];
 }
 
+// S = U Omega for one right-hand side (row stride G, G a multiple of 4):
+// items (RR rows, h quad); per four g one float4 of U per row and four float4
+// Omega rows give 16 RR FMAs.  Returns the thread's part of d = u.S.
+template <int RR>
+__device__ __forceinline__ float sigma_k1(const float* __restrict__ us, const float* __restrict__ Om_s,
+                                          float* __restrict__ S, int64_t row0, int tr, int G, int Gq) {
+  const int nhq = Gq >> 2;
+  const int ngrp = (tr + RR - 1) / RR;
+  const int nitems = ngrp * nhq;
+  float dl = 0.f;
+  for (int itm = threadIdx.x; itm < nitems; itm += blockDim.x) {
+    const int hq = itm % nhq, tg = itm / nhq;
+    const float* ur[RR];
+#pragma unroll
+    for (int a = 0; a < RR; ++a) {
+      const int t = RR * tg + a;
+      ur[a] = us + (int64_t)(t < tr ? t : RR * tg) * G;
+    }
+    float acc[RR][4];
+#pragma unroll
+    for (int a = 0; a < RR; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    for (int g0 = 0; g0 < G; g0 += 4) {
+      float4 uv[RR];
+#pragma unroll
+      for (int a = 0; a < RR; ++a) uv[a] = *reinterpret_cast<const float4*>(ur[a] + g0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 om = *reinterpret_cast<const float4*>(Om_s + (int64_t)(g0 + q) * Gq + 4 * hq);
+#pragma unroll
+        for (int a = 0; a < RR; ++a) {
+          const float x = q == 0 ? uv[a].x : q == 1 ? uv[a].y : q == 2 ? uv[a].z : uv[a].w;
+          acc[a][0] += x * om.x;
+          acc[a][1] += x * om.y;
+          acc[a][2] += x * om.z;
+          acc[a][3] += x * om.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < RR; ++a) {
+      const int t = RR * tg + a;
+      if (t < tr) {
+        // the h quad lies inside the row: G is a multiple of 4
+        *reinterpret_cast<float4*>(S + (row0 + t) * G + 4 * hq) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        const float4 uh = *reinterpret_cast<const float4*>(ur[a] + 4 * hq);
+        dl += acc[a][0] * uh.x + acc[a][1] * uh.y + acc[a][2] * uh.z + acc[a][3] * uh.w;
+      }
+    }
+  }
+  return dl;
+}
+
 // float32 with whole quads of right-hand sides: the TMA sigma step works on
 // float4 (four right-hand sides) per thread
 template <typename T, int JJ>
@@ -1173,55 +1227,15 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
         sigma_quads<1, JJ>(reinterpret_cast<const float*>(us), reinterpret_cast<const float*>(Om_s),
                            reinterpret_cast<float*>(S), row0, tr, G, Gq, GK, dsq);
     } else if (sizeof(T) == 4 && JJ == 1 && (G & 3) == 0) {
-      // one right-hand side, G a multiple of 4: item = (4 rows, h quad); per
-      // four g one float4 of U per row and four float4 Omega rows give 64 FMAs
-      constexpr int RR = 4;
-      const int ngrp = (tr + RR - 1) / RR;
-      const int nitems = ngrp * nhq;
+      // one right-hand side, G a multiple of 4: items (RR rows, h quad)
+      const int nhq1 = Gq >> 2;
       float dl = 0.f;
-      for (int itm = tid; itm < nitems; itm += blockDim.x) {
-        const int hq = itm % nhq, tg = itm / nhq;
-        const float* ur[RR];
-#pragma unroll
-        for (int a = 0; a < RR; ++a) {
-          const int t = RR * tg + a;
-          ur[a] = reinterpret_cast<const float*>(us) + (int64_t)(t < tr ? t : RR * tg) * G;
-        }
-        float acc[RR][4];
-#pragma unroll
-        for (int a = 0; a < RR; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-        for (int g0 = 0; g0 < G; g0 += 4) {
-          float4 uv[RR];
-#pragma unroll
-          for (int a = 0; a < RR; ++a) uv[a] = *reinterpret_cast<const float4*>(ur[a] + g0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 om = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Om_s) +
-                                                               (int64_t)(g0 + q) * Gq + 4 * hq);
-#pragma unroll
-            for (int a = 0; a < RR; ++a) {
-              const float x = q == 0 ? uv[a].x : q == 1 ? uv[a].y : q == 2 ? uv[a].z : uv[a].w;
-              acc[a][0] += x * om.x;
-              acc[a][1] += x * om.y;
-              acc[a][2] += x * om.z;
-              acc[a][3] += x * om.w;
-            }
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < RR; ++a) {
-          const int t = RR * tg + a;
-          if (t < tr) {
-            // h quad lies inside the row: G is a multiple of 4
-            *reinterpret_cast<float4*>(reinterpret_cast<float*>(S) + (row0 + t) * GK + 4 * hq) =
-                make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-            const float4 uh = *reinterpret_cast<const float4*>(ur[a] + 4 * hq);
-            dl += acc[a][0] * uh.x + acc[a][1] * uh.y + acc[a][2] * uh.z + acc[a][3] * uh.w;
-          }
-        }
-      }
+      if (((tr + 1) / 2) * nhq1 >= (int)blockDim.x)
+        dl = sigma_k1<2>(reinterpret_cast<const float*>(us), reinterpret_cast<const float*>(Om_s),
+                         reinterpret_cast<float*>(S), row0, tr, G, Gq);
+      else
+        dl = sigma_k1<1>(reinterpret_cast<const float*>(us), reinterpret_cast<const float*>(Om_s),
+                         reinterpret_cast<float*>(S), row0, tr, G, Gq);
       dsum += (double)dl;
     } else {
     // S = U Omega: item = (RI-row group, h quad, jj), RI x 4 outputs per item
