@@ -285,6 +285,15 @@ struct Inst {
     }
   }
 
+  // (Q e)[row r of the staged float64 tile, i, j] with e in the [col][K] layout
+  __device__ double qe_tile_d(const double* Qt, const double* e, int r, int i, int j) const {
+    const double* qp = Qt + r * d.np + sm.poff[i];
+    const double* ep = e + sm.poff[i] * K + j;
+    double s = 0.0;
+    for (int c = 0; c < sm.n_i[i]; ++c) s += qp[c] * ep[c * K];
+    return s;
+  }
+
   // Write the float32 accumulators transposed, eT[j * np + col], so that one
   // right-hand side's coefficients are contiguous (float4 reads in qe_tile).
   __device__ void store_acc_t(float (&acc)[kPairsPerThread][4], float* eT) const {
@@ -328,15 +337,6 @@ struct Inst {
     }
   }
 
-  // (Q e)[t, i, j] = sum over block i's columns
-  template <typename TQ, typename TE>
-  __device__ TE qe(const TQ* Q, const TE* e, int64_t t, int i, int j) const {
-    const TQ* qp = Q + d.q_off + t * d.np + sm.poff[i];
-    const TE* ep = e + sm.poff[i] * K + j;
-    TE s = 0;
-    for (int c = 0; c < sm.n_i[i]; ++c) s += (TE)qp[c] * ep[c * K];
-    return s;
-  }
 };
 
 template <int K, int kTR>
@@ -400,12 +400,18 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
     I.store_acc(acc64, e64);
     __syncthreads();
     double nrm = 0.0;
-    for (int64_t e = tid; e < nv; e += kBT) {
-      const int j = (int)(e % K), h = (int)((e / K) % G);
-      const int64_t t = e / GK;
-      const double rho = E64[e] - I.qe(P.q64, e64, t, h, j);
-      nrm += rho * rho;
-      g32[e] = (float)(-rho);
+    for (int64_t t0 = 0; t0 < M; t0 += kTR) {
+      const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
+      I.stage_q(P.q64, t0, tr, qt64);
+      __syncthreads();
+      for (int e = tid; e < tr * GK; e += kBT) {
+        const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
+        const int64_t gi = t0 * GK + e;
+        const double rho = E64[gi] - I.qe_tile_d(qt64, e64, r, h, j);
+        nrm += rho * rho;
+        g32[gi] = (float)(-rho);
+      }
+      __syncthreads();
     }
     cta_sum_strided<K>(nrm, sm.red, sm.colv);
     // ---- per-column decisions (reference: the single-instance refinement loop)
@@ -626,14 +632,19 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
     }
     I.store_acc(accp, e64);
     __syncthreads();
-    for (int64_t e = tid; e < nv; e += kBT) {
-      const int j = (int)(e % K), h = (int)((e / K) % G);
-      const int64_t t = e / GK;
-      const double dv = live[j] ? (double)w32[e] - I.qe(P.q64, e64, t, h, j) : 0.0;
-      d64[e] = dv;
-      w64[e] += dv;
+    for (int64_t t0 = 0; t0 < M; t0 += kTR) {
+      const int tr = (int)((M - t0) < kTR ? (M - t0) : kTR);
+      I.stage_q(P.q64, t0, tr, qt64);
+      __syncthreads();
+      for (int e = tid; e < tr * GK; e += kBT) {
+        const int j = e % K, rest = e / K, h = rest % G, r = rest / G;
+        const int64_t gi = t0 * GK + e;
+        const double dv = live[j] ? (double)w32[gi] - I.qe_tile_d(qt64, e64, r, h, j) : 0.0;
+        d64[gi] = dv;
+        w64[gi] += dv;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   // ---- b = R^-1 Q^T (y - Sigma w64)
   double accb[kPairsPerThread][4] = {};
