@@ -250,6 +250,8 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     h->kcap = k;
   }
   if (h->insts_k != k) {
+    // the descriptors are rewritten below: an earlier solve on this stream must be done
+    GS_CUDA_TRY(cudaStreamSynchronize(s));
     // first work order: most expensive steps first (cost ~ M (G^2 + 2 n'));
     // replaced by the measured times once the autotuner has run the batch
     std::vector<double> cost(h->count);
