@@ -57,6 +57,21 @@ def test_host_only_calls(libpath):
     assert L.glm_sur_setup(ctypes.byref(h), 0, 10, n_i, 1, 10, 1, None, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_setup(ctypes.byref(h), 2, 2, n_i, 1, 2, 1, None, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_solve(None, 1, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
+    # adjoint, restricted and batched entry points reject null handles / bad sizes on the host
+    assert L.glm_sur_backward(None, 1, 1, 1, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_solve_restricted(None, 1, 1, None, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_set_restrictions(None, 1, 1, 1, None) == _lib.GLM_SUR_INVALID_ARG
+    bh = ctypes.c_void_p()
+    g1 = (ctypes.c_int * 1)(2)
+    m1 = (ctypes.c_int * 1)(100)
+    nb = (ctypes.c_int * 2)(3, 4)
+    assert L.glm_sur_batch_setup(ctypes.byref(bh), 0, g1, m1, nb, 1, 1, None, None) == _lib.GLM_SUR_INVALID_ARG
+    g_big = (ctypes.c_int * 1)(33)    # more equations than a batched instance may have
+    assert L.glm_sur_batch_setup(ctypes.byref(bh), 1, g_big, m1, nb, 1, 1, None, None) == _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_batch_solve(None, 1, 8, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
+    steps = (ctypes.c_int * 1)()
+    assert L.glm_sur_batch_get_work(None, steps, None) == _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_batch_tile(None, None) <= 0
 
 
 def test_product_package_does_not_import_the_oracle():
