@@ -85,7 +85,9 @@ void glm_sur_default_opts(glm_sur_opts* opts);
  * step": the factorisations are computed once; Sec. 5.3: X_i = Q_i R_i).
  *
  *   out    : receives the new handle (host pointer).
- *   G      : number of equations (>= 1).
+ *   G      : number of equations, 1 <= G <= 1024.  Solves need G <= 156:
+ *            they stage Omega (G x ceil4(G) float64) in shared memory, and
+ *            glm_sur_solve returns GLM_SUR_INVALID_ARG for a larger G.
  *   M      : observations per equation (>= max n_i).
  *   n_i    : HOST array of G block widths, 1 <= n_i <= 64.
  *   X      : DEVICE, M x n column-major with leading dimension ldx >= M,

@@ -148,7 +148,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   const size_t om_bytes = sz * (size_t)gm.G * gm.Gq;
   const size_t row_bytes = sz * (size_t)gm.G * p.JJ;
   const size_t budget = 200 * 1024;
-  if (om_bytes + row_bytes > budget) return GLM_SUR_INVALID_ARG;   // G too large for the Sigma tile
+  if (gm.G > kMaxSolveG || om_bytes + row_bytes > budget) return GLM_SUR_INVALID_ARG;   // Omega must fit shared memory
   p.TR = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / 2 - std::min(om_bytes, budget / 2)) / row_bytes));
   if (p.TR < 1) p.TR = 1;
   p.sigma_smem = om_bytes + (size_t)p.TR * row_bytes;
