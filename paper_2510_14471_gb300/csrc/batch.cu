@@ -22,6 +22,7 @@ namespace {
 
 constexpr int kBT = 512;          // threads per CTA (one CTA per SM: 16 warps)
 constexpr int kPairsPerThread = 4;
+static_assert(kPairsPerThread * kBT >= kBatchMaxPairs, "every (column quad, rhs) pair needs a thread slot");
 
 // Shared memory of one CTA (carved from dynamic shared memory; sizes follow
 // the largest instance of the batch).

@@ -10,6 +10,7 @@ namespace glmsur {
 constexpr int kBatchMaxG = 32;      // equations per instance
 constexpr int kBatchMaxCols = 32;   // columns per block
 constexpr int kBatchMaxNp = 512;    // padded columns per instance
+constexpr int kBatchMaxPairs = 1024;  // column quads x right-hand sides an instance's CTA accumulates
 constexpr int kBatchMaxK = 8;       // right-hand sides per instance (1, 2, 4 or 8)
 
 // Device descriptor of one instance (offsets into the batch pools).

@@ -154,7 +154,7 @@ glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G
       np += round_up4(ni);
       h->r_elems += (int64_t)ni * ni;
     }
-    if (np > kBatchMaxNp || (np / 4) * kBatchMaxK > 4 * 256) { delete h; return GLM_SUR_INVALID_ARG; }
+    if (np > kBatchMaxNp || (np / 4) * kBatchMaxK > kBatchMaxPairs) { delete h; return GLM_SUR_INVALID_ARG; }
     for (int i = 0; i < g; ++i) qb[h->nblk + i].q_ld = np;
     h->G.push_back(g); h->M.push_back(mm); h->n.push_back(n); h->np.push_back(np); h->nq.push_back(np / 4);
     h->nblk += g;
@@ -233,7 +233,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
                                    double* relres, glm_sur_stream_t stream) {
   if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
   if (k != 1 && k != 2 && k != 4 && k != 8) return GLM_SUR_INVALID_ARG;
-  if (h->maxNq * k > 4 * 256) return GLM_SUR_INVALID_ARG;
+  if (h->maxNq * k > kBatchMaxPairs) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (k > h->kcap) {
     free_solve(h);
