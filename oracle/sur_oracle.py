@@ -334,7 +334,7 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     sqrt(eps) when written as r . (Pi r)).
     Stop a column when sqrt(c_{i+1}/c_1) <= tol (converged), when d_i <= 0 or
     is not finite (breakdown), when c has not reached a new minimum for W
-    steps (stagnation: "not anymore able to decrease", Sec. 3.2; c_i need
+    steps (stagnation: c no longer decreases, Sec. 3.2; c_i need
     not decrease monotonically, so a window over the running minimum is
     used), or at ``maxit``.  Always return
     z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
