@@ -84,3 +84,41 @@ def test_batched_instance_at_the_limits():
     assert all(s in (0, 4) for s in status), status
     for q, bq in zip((big, small), b):
         assert relcols(bq.cpu().numpy(), O.sur_gls_structured(q.X_blocks, q.Omega, q.Y)) <= TOL_B
+
+
+def test_scaling_omega_leaves_b_unchanged():
+    p = S.make_problem(G=5, M=700, n_i=[3, 4, 2, 5, 3], k=2, seed=509, omega="chol")
+    h = solver(p)
+    b1 = h.solve(p.Y).b.cpu().numpy()
+    h.set_omega(12.5 * p.Omega)
+    b2 = h.solve(p.Y).b.cpu().numpy()
+    assert relcols(b2, b1) <= TOL_B
+    assert relcols(b1, O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)) <= TOL_B
+
+
+def test_permuting_equations_permutes_b():
+    p = S.make_problem(G=5, M=700, n_i=[3, 4, 2, 5, 3], k=3, seed=510, omega="spectrum")
+    perm = [3, 0, 4, 2, 1]
+    q_blocks = [p.X_blocks[i] for i in perm]
+    q_omega = p.Omega[np.ix_(perm, perm)]
+    q_y = np.vstack([p.Y[i * p.M:(i + 1) * p.M] for i in perm])
+    from paper_2510_14471_gb300.sur import GlmSur
+    b = solver(p, precision="fp32_refine").solve(p.Y).b.cpu().numpy()
+    bq = GlmSur(q_blocks, q_omega, precision="fp32_refine").solve(q_y).b
+    offs = np.cumsum([0] + p.n_i)
+    b_perm = np.vstack([b[offs[i]:offs[i + 1]] for i in perm])
+    assert relcols(bq.cpu().numpy(), b_perm) <= TOL_B
+
+
+def test_one_handle_many_solves_and_precisions():
+    # k grows and shrinks and the precision changes on one handle; every
+    # result against the oracle
+    p = S.make_problem(G=4, M=900, n_i=[6, 3, 8, 5], k=8, seed=511, omega="wishart")
+    ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)
+    h = solver(p)
+    for precision, cols in (("fp64", [0, 1]), ("fp64", list(range(8))), ("fp32_refine", [2, 3, 4, 5]),
+                            ("fp32_refine", [7]), ("fp64", [6, 1, 0])):
+        h.set_options(precision=precision)
+        r = h.solve(p.Y[:, cols])
+        assert all(s in (0, 4) for s in r.status), (precision, cols, r.status)
+        assert relcols(r.b.cpu().numpy(), ref[:, cols]) <= TOL_B, (precision, cols)

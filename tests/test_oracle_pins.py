@@ -358,3 +358,32 @@ def test_planted_sign_error_in_sigma_apply_is_caught():
     Sg, _ = O.sur_dense(p.X_blocks, A)
     # (U Omega)_h = sum_g U_g omega_gh  <->  Sigma = Omega^T (x) I acting on vec(U)
     assert rel(op.sigma(u), Sg.T @ u) < 1e-14
+
+
+# ---------------------------------------------------------------- invariances
+
+def test_scaling_omega_leaves_b_and_scales_w():
+    # Sigma -> c Sigma: (w, b) -> (w / c, b) solves eq. (aug1) again
+    p = S.make_problem(G=3, M=20, n_i=[2, 3, 2], k=2, seed=71, omega="chol")
+    w, b = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
+    w2, b2 = O.aug_dense_solve(p.X_blocks, 7.5 * p.Omega, p.Y)
+    assert rel(b2, b) < 1e-12 and rel(7.5 * w2, w) < 1e-11
+    res = O.sur_pcg_aug(p.X_blocks, 7.5 * p.Omega, p.Y, tol=1e-14)
+    assert rel(res["b"], b) < 1e-10
+
+
+def test_permuting_equations_permutes_b():
+    # reordering the equations (blocks of X and y, rows/columns of Omega)
+    # reorders the blocks of b and nothing else
+    p = S.make_problem(G=4, M=25, n_i=[2, 3, 1, 2], k=1, seed=72, omega="chol")
+    perm = [2, 0, 3, 1]
+    Xp = [p.X_blocks[i] for i in perm]
+    Op = p.Omega[np.ix_(perm, perm)]
+    Yp = np.vstack([p.Y[i * p.M:(i + 1) * p.M] for i in perm])
+    b = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)
+    bp = O.sur_gls_structured(Xp, Op, Yp)
+    offs = np.cumsum([0] + p.n_i)
+    b_perm = np.vstack([b[offs[i]:offs[i + 1]] for i in perm])
+    assert rel(bp, b_perm) < 1e-12
+    res = O.sur_pcg_aug(Xp, Op, Yp, tol=1e-14)
+    assert rel(res["b"], b_perm) < 1e-10
