@@ -180,8 +180,8 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
  *               symmetric Omega, summed over the right-hand sides.
  *   iters, relres : DEVICE outputs (nullable, k): of the adjoint solve.
  * k must equal the k of the last solve; the handle must have no
- * restrictions and Omega must not have changed since that solve
- * (GLM_SUR_INVALID_ARG otherwise).  Afterwards glm_sur_get_status reports the
+ * restrictions, and neither Omega nor the precision or stagnation window
+ * may have changed since that solve (GLM_SUR_INVALID_ARG otherwise).  Afterwards glm_sur_get_status reports the
  * adjoint solve, and glm_sur_get_w still returns the forward w, so the call
  * may be repeated with another dL/db.
  */

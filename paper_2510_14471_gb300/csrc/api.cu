@@ -270,6 +270,7 @@ void free_workspace(glm_sur_ctx* h) {
   if (h->h_status) { delete[] h->h_status; h->h_status = nullptr; }
   h->kcap = 0;
   h->graph.reset();
+  h->has_w = false;   // the forward w went with the workspace (no adjoint without a new solve)
 }
 
 // Allocate every buffer a solve with k right-hand sides needs (both precisions).

@@ -87,6 +87,10 @@ def test_backward_rejects_mismatched_calls():
     h.set_omega(p.Omega)
     with pytest.raises(L.GlmSurError):              # Omega set after the solve
         h.backward(np.ones((p.n, 2)))
+    h.solve(p.Y)
+    h.set_options(precision="fp32_refine")
+    with pytest.raises(L.GlmSurError):              # precision changed after the solve
+        h.backward(np.ones((p.n, 2)))
 
 
 def _autograd_case(p, precision, target, Lfac):
