@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 PCG comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-reduced", action="store_true", help="skip the row-reduced comparison solve")
     ap.add_argument("--profile-reps", type=int, default=20)
     ap.add_argument("--workload", default="singular", choices=["singular", "batched", "constrained", "differentiable"],
                     help="singular: the headline workload; the others measure the batched, restricted and "
@@ -332,6 +333,29 @@ def run_ours(args, rank, world, local, pg):
                 "step_fp64_gflops": (2 * M * G * G * k + 4 * M * n * k) / (prof64[4] * 1e-3) / 1e9}
         h64.close()
 
+    # ---- the same solves on the row-reduced model (Remark rem:reduction)
+    reduced = None
+    if not args.no_reduced:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hr = GlmSur(p.X_blocks, p.Omega, precision=args.precision, tol=1e-13, reduce_rows=True, device=dev)
+        torch.cuda.synchronize()
+        setup_r = (time.perf_counter() - t0) * 1e3
+        Lr = hr.handle
+
+        def solve_r():
+            L.glm_sur_solve(Lr, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(), stream)
+
+        solve_r()
+        torch.cuda.synchronize()
+        ms_r, _ = timed(solve_r, max(1, args.steps), 1, local, None)
+        reduced = {"solves_per_s": 1e3 / ms_r, "ms_per_solve": ms_r, "setup_ms": setup_r,
+                   "rel_err_vs_beta_true": rel_err(b.t().cpu().numpy(), p.beta),
+                   "status": L.glm_sur_get_status(Lr, k), "iters_max": int(iters.cpu().numpy().max()),
+                   "rows": int(n), "note": "rows of every equation rotated onto range([X_1 ... X_G]); "
+                                           "one float64 product Q^T Y per solve"}
+        hr.close()
+
     # ---- CPU oracle baseline (rank 0, bounded sample)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -366,6 +390,7 @@ def run_ours(args, rank, world, local, pg):
                               "frac": ach_iter / hbm, "B_iter": b_iter, "ms": prof[4],
                               "kernel_ms": dict(zip(names, prof[:4]))},
             "fp64_pcg": fp64,
+            "row_reduced": reduced,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_sps, "unit": "solves/s", "h2d_bytes_per_step": int(m * k * 8),
                     "d2h_bytes_per_step": int(n * k * 8), "rel_err_max": e2e_err},

@@ -72,17 +72,20 @@ typedef struct {
   double inner_shift;     /* FP32_REFINE: the inner solves use Omega + s I with
                              s = inner_shift * max_i omega_ii (0 disables); the
                              float64 residual always uses Omega itself        */
+  int reduce_rows;        /* setup only: 1 = solve the row-reduced model of Remark
+                             rem:reduction (M' = n rows), when M >= 2 n and
+                             W = [X_1 ... X_G] has full column rank           */
 } glm_sur_opts;
 
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
- * max_refine 8, chunk 16, inner_shift 0.  A column that stops without
+ * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0.  A column that stops without
  * converging (stagnation, breakdown, maxit) returns its best saved iterate:
  * w is saved whenever c falls below a quarter of the c of the previous save. */
 void glm_sur_default_opts(glm_sur_opts* opts);
 
 /*
- * glm_sur_setup -- factor the regressors once (Sec. 3.2, "auxiliary GLM per
- * step": the factorisations are computed once; Sec. 5.3: X_i = Q_i R_i).
+ * glm_sur_setup -- factor the regressors once (Sec. 3.2: the factorisations
+ * the preconditioner needs do not change between steps; Sec. 5.3: X_i = Q_i R_i).
  *
  *   out    : receives the new handle (host pointer).
  *   G      : number of equations, 1 <= G <= 1024.  Solves need G <= 156:

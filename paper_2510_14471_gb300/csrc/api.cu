@@ -17,6 +17,7 @@
 #include "internal.h"
 #include "noalloc.h"
 #include "pcg.h"
+#include "reduce.h"
 #include "rglm.h"
 
 namespace glmsur {
@@ -106,6 +107,12 @@ struct glm_sur_ctx {
   double* gC = nullptr;        // kc x k restriction rows of g
   int rcap = 0;                // k capacity of cbuf / fbuf / gC
   bool w_restricted = false;   // w64 came from a restricted solve
+  // row reduction (Remark rem:reduction): the solves run on `sub`, the model
+  // with the n rows Q^T y_i of every equation
+  glm_sur_ctx* sub = nullptr;
+  double* Qw = nullptr;        // M x n column-major orthonormal basis of range(W)
+  double* yred = nullptr;      // reduced responses / gradients, (G n) x k column-major
+  int64_t yred_cap = 0;
   // adjoint (glm_sur_backward)
   double* wfwd = nullptr;      // the forward w while the adjoint solve runs
   double* lam1 = nullptr;      // particular solution lam_1 = Q R^-T dL/db
@@ -514,6 +521,104 @@ glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, 
   return GLM_SUR_OK;
 }
 
+// Remark rem:reduction.  Q (M x n) orthonormal with range(Q) = range(W), by
+// Cholesky QR twice; R_W = L2^T L1^T (n x n, upper), so X_i = Q R_W[:, block i]
+// and the reduced model has X_i' = R_W[:, block i] and y_i' = Q^T y_i (M' = n).
+// GLM_SUR_RANK_DEFICIENT (nothing kept) when W^T W is not positive definite.
+glm_sur_status setup_reduced(glm_sur_t* out, int G, int64_t M, const int* n_i, int n, const double* X, int64_t ldx,
+                             const double* Omega, glm_sur_opts o, cudaStream_t s) {
+  double *G1 = nullptr, *Li1 = nullptr, *G2 = nullptr, *Li2 = nullptr, *Q1 = nullptr, *Q = nullptr, *Rw = nullptr;
+  int* flag = nullptr;
+  auto release = [&]() {
+    dfree(G1); dfree(Li1); dfree(G2); dfree(Li2); dfree(Q1); dfree(Rw); dfree(flag);
+  };
+  const size_t nn = (size_t)n * n, Mn = (size_t)M * n;
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&G1, nn)) != cudaSuccess || (e = dalloc(&Li1, nn)) != cudaSuccess ||
+      (e = dalloc(&G2, nn)) != cudaSuccess || (e = dalloc(&Li2, nn)) != cudaSuccess ||
+      (e = dalloc(&Q1, Mn)) != cudaSuccess || (e = dalloc(&Q, Mn)) != cudaSuccess ||
+      (e = dalloc(&Rw, nn)) != cudaSuccess || (e = dalloc(&flag, 1)) != cudaSuccess) {
+    release();
+    dfree(Q);
+    set_last_error(e, "cudaMalloc (row reduction)", __FILE__, __LINE__);
+    return e == cudaErrorMemoryAllocation ? GLM_SUR_OOM : GLM_SUR_CUDA_ERROR;
+  }
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  // W^T W = L1 L1^T ;  Q1 = W L1^-T
+  // a pivot below 64 n eps of the largest diagonal entry: W is treated as rank deficient
+  const double piv_tol = 64.0 * n * 2.220446049250313e-16;
+  launch_dgemm(n, n, M, X, ldx, 1, X, 1, ldx, G1, n, 1, s);
+  cholesky_lower(n, G1, flag, piv_tol, s);
+  launch_zero_upper(n, G1, s);
+  launch_tri_inverse(n, G1, Li1, s);
+  launch_dgemm((int)M, n, n, X, 1, ldx, Li1, 1, n, Q1, 1, M, s);
+  // Q1^T Q1 = L2 L2^T ;  Q = Q1 L2^-T
+  launch_dgemm(n, n, M, Q1, M, 1, Q1, 1, M, G2, n, 1, s);
+  cholesky_lower(n, G2, flag, piv_tol, s);
+  launch_zero_upper(n, G2, s);
+  launch_tri_inverse(n, G2, Li2, s);
+  launch_dgemm((int)M, n, n, Q1, 1, M, Li2, 1, n, Q, 1, M, s);
+  // R_W = L2^T L1^T (column-major n x n: the reduced regressors)
+  launch_dgemm(n, n, n, G2, 1, n, G1, 1, n, Rw, 1, n, s);
+  int hflag = 0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || hflag) {
+    release();
+    dfree(Q);
+    if (e != cudaSuccess) {
+      set_last_error(e, "row reduction", __FILE__, __LINE__);
+      return GLM_SUR_CUDA_ERROR;
+    }
+    return GLM_SUR_RANK_DEFICIENT;
+  }
+  glm_sur_opts so = o;
+  so.reduce_rows = 0;
+  glm_sur_t sub = nullptr;
+  glm_sur_status rc = glm_sur_setup(&sub, G, n, n_i, Rw, n, Omega, &so, reinterpret_cast<glm_sur_stream_t>(s));
+  cudaStreamSynchronize(s);
+  release();
+  if (rc != GLM_SUR_OK) {
+    dfree(Q);
+    return rc;
+  }
+  glm_sur_ctx* h = new glm_sur_ctx();
+  h->opts = o;
+  h->sub = sub;
+  h->Qw = Q;
+  h->gm.G = G;
+  h->gm.Gq = round_up4(G);
+  h->gm.M = M;
+  h->gm.n = n;
+  h->n_i.assign(n_i, n_i + G);
+  h->launches = 11;
+  *out = h;
+  return GLM_SUR_OK;
+}
+
+// Reduced responses of every right-hand side: yred[(j G + i) n + r] = (Q^T y_ij)[r]
+glm_sur_status rotate_in(glm_sur_ctx* h, const double* Y, int64_t ldy, int k, cudaStream_t s) {
+  const int64_t M = h->gm.M, n = h->gm.n, G = h->gm.G;
+  const int64_t need = G * n * k;
+  if (need > h->yred_cap) {
+    dfree(h->yred);
+    h->yred_cap = 0;
+    GS_CUDA_TRY(dalloc(&h->yred, (size_t)need));
+    h->yred_cap = need;
+  }
+  if (ldy == M * G) {
+    launch_dgemm((int)n, (int)(G * k), M, h->Qw, M, 1, Y, 1, M, h->yred, 1, n, s);
+    h->launches += 1;
+  } else {
+    for (int j = 0; j < k; ++j)
+      launch_dgemm((int)n, (int)G, M, h->Qw, M, 1, Y + (int64_t)j * ldy, 1, M, h->yred + j * G * n, 1, n, s);
+    h->launches += k;
+  }
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -531,6 +636,7 @@ void glm_sur_default_opts(glm_sur_opts* o) {
   o->max_refine = 8;
   o->chunk = 16;
   o->inner_shift = 0.0;
+  o->reduce_rows = 0;
 }
 
 const char* glm_sur_status_string(glm_sur_status s) {
@@ -567,6 +673,16 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   if (opts) o = *opts;
   if (validate_opts(&o) != GLM_SUR_OK) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.reduce_rows) {
+    int64_t n = 0;
+    for (int i = 0; i < G; ++i) n += n_i[i];
+    if (M >= 2 * n) {
+      glm_sur_status rr = setup_reduced(out, G, M, n_i, (int)n, X, ldx, Omega, o, s);
+      if (rr != GLM_SUR_RANK_DEFICIENT) return rr;
+      // W without full column rank: the unreduced model below
+    }
+    o.reduce_rows = 0;
+  }
 
   glm_sur_ctx* h = new glm_sur_ctx();
   h->opts = o;
@@ -675,6 +791,7 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
 }
 
 glm_sur_status glm_sur_get_setup_status(glm_sur_t h) {
+  if (h && h->sub) return glm_sur_get_setup_status(h->sub);
   if (!h) return GLM_SUR_INVALID_ARG;
   int flags = 0;
   GS_CUDA_TRY(cudaMemcpy(&flags, h->setup_flags, sizeof(int), cudaMemcpyDeviceToHost));
@@ -684,6 +801,7 @@ glm_sur_status glm_sur_get_setup_status(glm_sur_t h) {
 }
 
 glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_stream_t stream) {
+  if (h && h->sub) return glm_sur_set_omega(h->sub, Omega, stream);
   if (!h || !Omega) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const Geom& gm = h->gm;
@@ -699,6 +817,13 @@ glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_strea
 }
 
 glm_sur_status glm_sur_set_opts(glm_sur_t h, const glm_sur_opts* opts) {
+  if (h && h->sub && opts) {
+    glm_sur_opts so = *opts;
+    so.reduce_rows = 0;
+    glm_sur_status rc = glm_sur_set_opts(h->sub, &so);
+    if (rc == GLM_SUR_OK) h->opts = *opts;
+    return rc;
+  }
   if (!h || !opts) return GLM_SUR_INVALID_ARG;
   if (validate_opts(opts) != GLM_SUR_OK) return GLM_SUR_INVALID_ARG;
   const bool need_q32 = opts->precision == GLM_SUR_PREC_FP32_REFINE && !h->Q32;
@@ -865,6 +990,13 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
 glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
                           int64_t ldb, int* iters, double* relres, cudaStream_t s) {
   if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  if (h->sub) {
+    // Remark rem:reduction: the same estimate from the n rotated rows
+    if (k < 1 || k > kMaxRhs || ldy < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
+    glm_sur_status rc = rotate_in(h, Y, ldy, k, s);
+    if (rc != GLM_SUR_OK) return rc;
+    return solve_impl(h->sub, h->yred, (int64_t)h->gm.G * h->gm.n, d, ldd, k, b, ldb, iters, relres, s);
+  }
   const Geom& gm = h->gm;
   const int64_t m = gm.M * gm.G;
   if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
@@ -915,13 +1047,28 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
 glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd,
                                         int k, double* b, int64_t ldb, int* iters, double* relres,
                                         glm_sur_stream_t stream) {
-  if (!h || h->kc == 0) return GLM_SUR_INVALID_ARG;
+  if (!h || (h->sub ? h->sub->kc : h->kc) == 0) return GLM_SUR_INVALID_ARG;
   return solve_impl(h, Y, ldy, d, ldd, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
 }
 
 glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY, int64_t ldy,
                                 double* dL_dOmega, int64_t ldo, int* iters, double* relres, glm_sur_stream_t stream) {
   if (!h || !dL_db || (!dL_dY && !dL_dOmega)) return GLM_SUR_INVALID_ARG;
+  if (h->sub) {
+    // the adjoint of the reduced model; dL/dy = Q dL/dy' (the rows outside
+    // range(W) have lam = 0) and dL/dOmega is the reduced model's
+    const int64_t M = h->gm.M, n = h->gm.n, G = h->gm.G;
+    if (k < 1 || k > kMaxRhs || (dL_dY && ldy < M * G) || G * n * k > h->yred_cap) return GLM_SUR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    glm_sur_status rc = glm_sur_backward(h->sub, dL_db, ldg, k, dL_dY ? h->yred : nullptr, G * n, dL_dOmega, ldo,
+                                         iters, relres, stream);
+    if (rc != GLM_SUR_OK || !dL_dY) return rc;
+    for (int j = 0; j < k; ++j)
+      launch_dgemm((int)M, (int)G, n, h->Qw, 1, M, h->yred + j * G * n, 1, n, dL_dY + (int64_t)j * ldy, 1, M, s);
+    h->launches += k;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GLM_SUR_OK;
+  }
   const Geom& gm = h->gm;
   const int64_t m = gm.M * gm.G;
   if (k < 1 || k != h->last_k || !h->has_w || h->w_restricted || h->kc > 0 || ldg < gm.n || (dL_dY && ldy < m) || (dL_dOmega && ldo < gm.G))
@@ -964,6 +1111,7 @@ glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, i
 }
 
 glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ldc, int kc, glm_sur_stream_t stream) {
+  if (h && h->sub) return glm_sur_set_restrictions(h->sub, C, ldc, kc, stream);
   if (!h || kc < 0 || (kc > 0 && (!C || ldc < kc))) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const Geom& gm = h->gm;
@@ -988,6 +1136,7 @@ glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ld
 }
 
 glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
+  if (h && h->sub) return glm_sur_get_status(h->sub, status, k);
   if (!h || !status || k < 1 || k > h->last_k) return GLM_SUR_INVALID_ARG;
   GS_CUDA_TRY(cudaDeviceSynchronize());
   GS_CUDA_TRY(cudaMemcpy(status, h->d_status_final, k * sizeof(int), cudaMemcpyDeviceToHost));
@@ -1006,6 +1155,7 @@ glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
 }
 
 glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream) {
+  if (h && h->sub) return GLM_SUR_INVALID_ARG;   // w of the unreduced rows is not formed
   if (!h || !w || !h->has_w || ldw < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_layout_to_colmajor<double>(h->gm, h->last_k, h->w64, w, ldw, s);
@@ -1014,6 +1164,7 @@ glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream
 }
 
 glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* R, glm_sur_stream_t stream) {
+  if (h && h->sub) return GLM_SUR_INVALID_ARG;   // the factors belong to the reduced model
   if (!h || (Q && ldq < h->gm.M)) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const Geom& gm = h->gm;
@@ -1030,9 +1181,13 @@ glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* 
   return GLM_SUR_OK;
 }
 
-int64_t glm_sur_launch_count(glm_sur_t h) { return h ? h->launches : -1; }
+int64_t glm_sur_launch_count(glm_sur_t h) {
+  if (!h) return -1;
+  return h->launches + (h->sub ? glm_sur_launch_count(h->sub) : 0);
+}
 
 glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_stream_t stream) {
+  if (h && h->sub) return glm_sur_profile_steps(h->sub, reps, ms, stream);
   if (!h || !ms || reps < 1 || h->last_k < 1 || h->plan_k != h->last_k) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int k = h->last_k;
@@ -1099,6 +1254,7 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
 
 glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb,
                                   glm_sur_stream_t stream) {
+  if (h && h->sub) return GLM_SUR_INVALID_ARG;   // a rotation needs device workspace
   if (!h || !Y || !b || k < 1 || k > kMaxRhs) return GLM_SUR_INVALID_ARG;
   const Geom& gm = h->gm;
   if (ldy < gm.M * gm.G || ldb < gm.n) return GLM_SUR_INVALID_ARG;
@@ -1108,6 +1264,14 @@ glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int
 
 void glm_sur_destroy(glm_sur_t h) {
   if (!h) return;
+  if (h->sub) {
+    glm_sur_destroy(h->sub);
+    cudaDeviceSynchronize();
+    dfree(h->Qw);
+    dfree(h->yred);
+    delete h;
+    return;
+  }
   cudaDeviceSynchronize();
   free_workspace(h);
   dfree(h->Q64); dfree(h->Q32); dfree(h->R); dfree(h->Om64); dfree(h->Om32); dfree(h->setup_flags);

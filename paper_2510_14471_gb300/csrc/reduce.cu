@@ -1,0 +1,123 @@
+// Row reduction of the SUR model (Remark rem:reduction).  With W = [X_1 ...
+// X_G] (M x n) = Q R_W, Q orthonormal (M x n), the rows of the model outside
+// range(W) carry no regressor; Sigma = Omega (x) I_M acts on every row alike,
+// so rotating the rows of each equation by [Q Q_perp] splits eq. (aug1) into
+// the reduced model (X_i' = R_W[:, block i], y_i' = Q^T y_i, M' = n rows)
+// and rows that do not touch b.  b of the reduced model is b of the model.
+// Q comes from Cholesky QR twice: W^T W = L1 L1^T, Q1 = W L1^-T, then the same
+// on Q1; R_W = L2^T L1^T.  The products below are float64 (the responses and
+// the basis are float64 data).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "reduce.h"
+
+namespace glmsur {
+
+namespace {
+
+constexpr int kTM = 64, kTN = 64, kTK = 16;   // output tile and depth step of the float64 product
+
+// 256 threads, 4 x 4 outputs each; A and B tiles staged in shared memory.
+__global__ void __launch_bounds__(256)
+k_dgemm(int m, int n, int64_t kdim, const double* __restrict__ A, int64_t ars, int64_t acs,
+        const double* __restrict__ B, int64_t brs, int64_t bcs, double* __restrict__ C, int64_t crs, int64_t ccs) {
+  __shared__ double As[kTK][kTM + 1];
+  __shared__ double Bs[kTK][kTN + 1];
+  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int64_t p0 = 0; p0 < kdim; p0 += kTK) {
+    // the depth index runs fastest across threads: unit-stride operands load coalesced
+    for (int e = threadIdx.x; e < kTK * kTM; e += 256) {
+      const int pp = e % kTK, ii = e / kTK;
+      const int64_t p = p0 + pp;
+      const int i = i0 + ii;
+      As[pp][ii] = (i < m && p < kdim) ? A[(int64_t)i * ars + p * acs] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kTK * kTN; e += 256) {
+      const int pp = e % kTK, jj = e / kTK;
+      const int64_t p = p0 + pp;
+      const int j = j0 + jj;
+      Bs[pp][jj] = (j < n && p < kdim) ? B[p * brs + (int64_t)j * bcs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int pp = 0; pp < kTK; ++pp) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[pp][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[pp][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+    if (i >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (j < n) C[(int64_t)i * crs + (int64_t)j * ccs] = acc[r][c];
+    }
+  }
+}
+
+// Column j of L^-1 (forward substitution L y = e_j; one CTA per column).
+__global__ void __launch_bounds__(256) k_tri_inverse_cols(int n, const double* __restrict__ L,
+                                                          double* __restrict__ Linv) {
+  extern __shared__ double y[];
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = 0.0;
+  __syncthreads();
+  for (int i = j; i < n; ++i) {
+    double part = 0.0;
+    for (int s = j + threadIdx.x; s < i; s += blockDim.x) part += L[(int64_t)i * n + s] * y[s];
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      y[i] = ((i == j ? 1.0 : 0.0) - t) / L[(int64_t)i * n + i];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Linv[(int64_t)i * n + j] = y[i];
+}
+
+__global__ void k_zero_upper(int n, double* __restrict__ A) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  if (j > i) A[idx] = 0.0;
+}
+
+}  // namespace
+
+void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int64_t acs, const double* B,
+                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(n, kTN), (unsigned)ceil_div(m, kTM));
+  k_dgemm<<<grid, 256, 0, s>>>(m, n, kdim, A, ars, acs, B, brs, bcs, C, crs, ccs);
+}
+
+cudaError_t launch_tri_inverse(int n, const double* L, double* Linv, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)n;
+  cudaError_t e = cudaFuncSetAttribute(k_tri_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tri_inverse_cols<<<n, 256, smem, s>>>(n, L, Linv);
+  return cudaGetLastError();
+}
+
+void launch_zero_upper(int n, double* A, cudaStream_t s) {
+  k_zero_upper<<<(unsigned)ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, A);
+}
+
+}  // namespace glmsur

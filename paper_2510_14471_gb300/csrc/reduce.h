@@ -1,0 +1,24 @@
+// Row reduction of the SUR model (Remark rem:reduction): an orthonormal
+// basis Q of range(W), W = [X_1 ... X_G], by Cholesky QR twice, and the
+// float64 products that move responses and gradients between the M rows of
+// the model and the n rows of the reduced one.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace glmsur {
+
+// C(i, j) = sum_p A(i, p) B(p, j) for i < m, j < n, p < kdim, float64, with
+// A(i, p) at A[i * ars + p * acs], B(p, j) at B[p * brs + j * bcs] and C(i, j)
+// at C[i * crs + j * ccs] (any layout: strides carry transposes).
+void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int64_t acs, const double* B,
+                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s);
+
+// Linv = L^-1 for a row-major lower-triangular n x n L (its strict upper
+// triangle is ignored); Linv row-major with zeros above the diagonal.
+cudaError_t launch_tri_inverse(int n, const double* L, double* Linv, cudaStream_t s);
+
+// Zero the strict upper triangle of a row-major n x n matrix.
+void launch_zero_upper(int n, double* A, cudaStream_t s);
+
+}  // namespace glmsur

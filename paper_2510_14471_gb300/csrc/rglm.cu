@@ -41,14 +41,20 @@ __global__ void k_rglm_normal(int n, int kc, const double* __restrict__ C, int64
 }
 
 // In-place Cholesky N = L L^T (lower triangle of the row-major N), one CTA.
-// flag |= 1 when a pivot is not positive (N singular: C and the X_i do not
-// determine b).
-__global__ void __launch_bounds__(1024) k_rglm_cholesky(int n, double* __restrict__ N, int* flag) {
-  __shared__ double piv;
+// flag |= 1 when a pivot is not above rel_tol times the largest diagonal
+// entry of N (N singular: C and the X_i do not determine b).
+__global__ void __launch_bounds__(1024) k_rglm_cholesky(int n, double* __restrict__ N, int* flag, double rel_tol) {
+  __shared__ double piv, floor_s;
+  if (threadIdx.x == 0) {
+    double dmax = 0.0;
+    for (int j = 0; j < n; ++j) dmax = fmax(dmax, N[(int64_t)j * n + j]);
+    floor_s = rel_tol * dmax;
+  }
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       const double v = N[(int64_t)j * n + j];
-      piv = (v > 0.0 && isfinite(v)) ? sqrt(v) : 0.0;
+      piv = (v > floor_s && v > 0.0 && isfinite(v)) ? sqrt(v) : 0.0;
       if (piv == 0.0) atomicOr(flag, 1);
       N[(int64_t)j * n + j] = piv;
     }
@@ -214,7 +220,7 @@ cudaError_t rglm_factor(const Geom& gm, const double* R, const double* C, int64_
   const int n = gm.n;
   k_rglm_normal<<<(unsigned)ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, kc, C, ldc, col_blk, gm.d_off, gm.d_n_i, R,
                                                                       gm.d_r_off, N);
-  k_rglm_cholesky<<<1, 1024, 0, s>>>(n, N, flag);
+  k_rglm_cholesky<<<1, 1024, 0, s>>>(n, N, flag, 0.0);
   const size_t smem = sizeof(double) * (size_t)n;
   cudaError_t e = cudaFuncSetAttribute(k_rglm_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -222,6 +228,11 @@ cudaError_t rglm_factor(const Geom& gm, const double* R, const double* C, int64_
   e = cudaFuncSetAttribute(k_rglm_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_rglm_inverse_cols<<<n, 256, smem, s>>>(n, N, Minv);
+  return cudaGetLastError();
+}
+
+cudaError_t cholesky_lower(int n, double* N, int* flag, double rel_tol, cudaStream_t s) {
+  k_rglm_cholesky<<<1, 1024, 0, s>>>(n, N, flag, rel_tol);
   return cudaGetLastError();
 }
 
