@@ -48,7 +48,7 @@ def test_host_only_calls(libpath):
     from paper_2510_14471_gb300 import _lib
     L = _lib.lib()
     o = _lib.default_opts()
-    assert o.precision == 0 and o.chunk % 2 == 0 and o.tol > 0
+    assert o.precision == 0 and o.chunk % 2 == 0 and o.tol > 0 and o.reduce_rows == 0
     assert L.glm_sur_status_string(2).decode().startswith("rank")
     assert "sm_103a" in _lib.glm_sur_version()
     # argument validation happens before any device work

@@ -387,3 +387,17 @@ def test_permuting_equations_permutes_b():
     assert rel(bp, b_perm) < 1e-12
     res = O.sur_pcg_aug(Xp, Op, Yp, tol=1e-14)
     assert rel(res["b"], b_perm) < 1e-10
+
+
+def test_row_reduction_leaves_b_unchanged():
+    # Remark rem:reduction: rotating the rows of every equation onto range(W),
+    # W = [X_1 ... X_G], gives a model with the same estimate (dense brute force
+    # on both models; singular and regular Omega)
+    for seed, omega, rank in ((73, "chol", None), (74, "lowrank", 2)):
+        p = S.make_problem(G=3, M=30, n_i=[2, 3, 2], k=2, seed=seed, omega=omega, rank=rank)
+        B = O.range_basis(np.hstack(p.X_blocks))
+        Xr = [B.T @ x for x in p.X_blocks]
+        Yr = np.vstack([B.T @ p.Y[i * p.M:(i + 1) * p.M] for i in range(p.G)])
+        _, b = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
+        _, br = O.aug_dense_solve(Xr, p.Omega, Yr)
+        assert rel(br, b) < 1e-10
