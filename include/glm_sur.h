@@ -197,13 +197,16 @@ glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, i
 glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k);
 
 /* Copies the float64 w of the last solve (m x k column-major, DEVICE, ldw >= m)
- * into a caller buffer; Sigma w is the GLM residual of eq. (aug1). */
+ * into a caller buffer; Sigma w is the GLM residual of eq. (aug1).
+ * GLM_SUR_INVALID_ARG on a handle set up with reduce_rows (w of the rows
+ * outside range(W) is not formed). */
 glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream);
 
 /* Copies the factors of glm_sur_setup into caller buffers (both DEVICE):
  * Q (M x n column-major, ldq >= M): the thin Q_i side by side, [Q_1 ... Q_G];
  * R (sum_i n_i^2 doubles): R_i row-major n_i x n_i, blocks in order.
- * Either pointer may be NULL. */
+ * Either pointer may be NULL.  GLM_SUR_INVALID_ARG on a handle set up with
+ * reduce_rows (its factors are those of the reduced model). */
 glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* R, glm_sur_stream_t stream);
 
 /* Number of kernel launches (including the nodes of replayed CUDA graphs)
@@ -241,6 +244,7 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
  * run at the same time on the GPU (different streams without ordering)
  * race and must be serialised by the caller.  Nothing in the array needs
  * clearing between calls: each call writes every entry it reads.
+ * GLM_SUR_INVALID_ARG on a handle set up with reduce_rows.
  */
 glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int k,
                                   double* b, int64_t ldb, glm_sur_stream_t stream);
