@@ -73,8 +73,9 @@ typedef struct {
                              s = inner_shift * max_i omega_ii (0 disables); the
                              float64 residual always uses Omega itself        */
   int reduce_rows;        /* setup only: 1 = solve the row-reduced model of Remark
-                             rem:reduction (M' = n rows), when M >= 2 n and
-                             W = [X_1 ... X_G] has full column rank           */
+                             rem:reduction (M' = n rows), when M >= 2 n,
+                             n <= 2048 and W = [X_1 ... X_G] has full column
+                             rank (otherwise the model is kept whole)         */
 } glm_sur_opts;
 
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,

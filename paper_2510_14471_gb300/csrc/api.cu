@@ -676,7 +676,8 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   if (o.reduce_rows) {
     int64_t n = 0;
     for (int i = 0; i < G; ++i) n += n_i[i];
-    if (M >= 2 * n) {
+    // the basis costs a one-CTA Cholesky of n x n (n^3 / 3 flops): kept to n <= 2048
+    if (M >= 2 * n && n <= kMaxReducedCols) {
       glm_sur_status rr = setup_reduced(out, G, M, n_i, (int)n, X, ldx, Omega, o, s);
       if (rr != GLM_SUR_RANK_DEFICIENT) return rr;
       // W without full column rank: the unreduced model below

@@ -12,6 +12,7 @@ namespace glmsur {
 constexpr int kMaxBlockCols = 64;   // max n_i (TSQR leaves hold <= 256 x 32 or 128 x 64)
 constexpr int kMaxRhs = 64;         // max k
 constexpr int kMaxG = 1024;         // max number of equations of a handle
+constexpr int kMaxReducedCols = 2048;   // largest n of a row-reduced model (its setup Cholesky is n^3 / 3)
 constexpr int kMaxSolveG = 156;     // max equations of a solve: float64 Omega and one row tile of
                                     // eight right-hand sides within 200 KB of shared memory
 
