@@ -336,13 +336,8 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     is not finite (breakdown), when c has not reached a new minimum for W
     steps (stagnation: c no longer decreases, Sec. 3.2; c_i need
     not decrease monotonically, so a window over the running minimum is
-    used), or at ``maxit``.  Always return
+    used), or at ``maxit``.  Every column returns its last iterate w and
     z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
-    A column that stops without converging returns the w of its best
-    snapshot: w is saved whenever c falls below a quarter of the c at the
-    previous save, and restored if that saved c is below the c at the stop
-    (a singular A = Q_N^T Sigma Q_N lets the recursive residual grow again
-    after its rounding floor, so the last iterate is not the best one).
     Returns dict(b, w, iters, status, relres[, history])."""
     op = ops if ops is not None else SurOps(X_blocks, Omega)
     m = op.G * op.M
@@ -366,9 +361,6 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     relres = np.where(c1 > 0, 1.0, 0.0)
     cbest = c.copy()
     itbest = np.zeros(k, dtype=int)
-    csnap = c.copy()
-    wsnap = w.copy()
-    cstop = np.full(k, np.inf)
     hist = {"w": [w.copy()], "r": [r.copy()], "u": [u.copy()], "c": [c.copy()]} if record else None
     for it in range(1, maxit + 1):
         if not active.any():
@@ -385,10 +377,6 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
         Pr = op.pi(r)
         c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)  # step 8
         iters = iters + active
-        snap = active & (c_new < 0.25 * csnap)
-        csnap = np.where(snap, c_new, csnap)
-        wsnap[:, snap] = w[:, snap]
-        cstop = np.where(active, c_new, cstop)
         rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
         relres = np.where(active, rr, relres)
         bad_c = active & (~np.isfinite(c_new) | (c_new < 0))
@@ -413,10 +401,6 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
         if record:
             hist["w"].append(w.copy()); hist["r"].append(r.copy())
             hist["u"].append(u.copy()); hist["c"].append(c_new.copy())
-    for j in range(k):
-        if status[j] != STATUS_CONVERGED and not (cstop[j] <= csnap[j]):
-            w[:, j] = wsnap[:, j]
-            relres[j] = np.sqrt(csnap[j] / c1[j]) if c1[j] > 0 else 0.0
     b = op.xstar_t(Y - op.sigma(w))                           # step 10
     out = dict(b=b, w=w, iters=iters, status=list(status), relres=relres)
     if record:
