@@ -239,9 +239,13 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
  *   b  : DEVICE output, n x k column-major, ldb >= n.
  * Limit: (n' * k) * 2 <= 524288 doubles, n' = sum_i 4*ceil(n_i/4); larger
  * requests return GLM_SUR_INVALID_ARG before any device work.
+ * Call it with the handle's device current (GLM_SUR_INVALID_ARG otherwise).
  * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that may
+ * (cudaGetSymbolAddress) with that device current; under CUDA's lazy module
+ * loading that first call also loads the library's module that holds the
+ * array (which reserves the 4 MiB on the device and may synchronise), so
+ * make that first call outside any latency-critical region and before any
+ * stream capture.  All calls share the array: calls that may
  * run at the same time on the GPU (different streams without ordering)
  * race and must be serialised by the caller.  Nothing in the array needs
  * clearing between calls: each call writes every entry it reads.

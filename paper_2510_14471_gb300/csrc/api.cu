@@ -1260,6 +1260,9 @@ glm_sur_status glm_sur_ols_static(glm_sur_t h, const double* Y, int64_t ldy, int
   const Geom& gm = h->gm;
   if (ldy < gm.M * gm.G || ldb < gm.n) return GLM_SUR_INVALID_ARG;
   if ((long long)gm.np * k * 2 > kOlsScratchDoubles) return GLM_SUR_INVALID_ARG;
+  // the scratch address is looked up on the current device: it must be the handle's
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->dev) return GLM_SUR_INVALID_ARG;
   return ols_static(gm, h->Q64, h->R, Y, ldy, k, b, ldb, h->sms, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -1,5 +1,5 @@
 """The allocation-free entry point glm_sur_ols_static, called through the C
-ABI, against the existing solver.
+ABI, against the existing solver and the oracle's per-block least squares.
 
 glm_sur_ols_static returns the per-block least-squares estimate
 R_i^-1 Q_i^T y_i from a handle's factors using only the library's fixed
@@ -13,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import sur_oracle as O
 from synth import sur_inputs as S
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +35,7 @@ def test_ols_static_matches_solver_on_two_calls_in_a_row():
     p = S.make_problem(G=6, M=3001, n_i=[3, 8, 5, 12, 7, 4], k=4, seed=71, omega="diag")
     h = GlmSur(p.X_blocks, p.Omega, precision="fp64", tol=1e-13)
     ref = h.solve(p.Y).b.cpu().numpy()                      # existing entry point
+    ols = O.ols_blocks(p.X_blocks, p.Y)                     # Sec. 1: b_i = (X_i^T X_i)^-1 X_i^T y_i
     Ycm = torch.as_tensor(np.ascontiguousarray(p.Y.T), device="cuda")
     m, k = p.Y.shape
     stream = torch.cuda.current_stream().cuda_stream
@@ -45,6 +47,8 @@ def test_ols_static_matches_solver_on_two_calls_in_a_row():
         got = b.t().cpu().numpy()
         err = np.max(np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0))
         assert err <= TOL_B, (call, err)
+        err_o = np.max(np.linalg.norm(got - ols, axis=0) / np.linalg.norm(ols, axis=0))
+        assert err_o <= TOL_B, (call, err_o)
 
 
 def test_ols_static_rejects_requests_beyond_its_scratch():
