@@ -60,14 +60,15 @@ def test_batch_singular_and_edge_instances():
         assert relcols(b[j], O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)) <= TOL_B, j
 
 
-def test_full_batch_workload_sampled_instances():
-    # 2048 instances, G ~ U{2..12}, M ~ U{200..4000}, n_i ~ U{2..10}, k = 8
+def test_full_batch_workload_every_instance():
+    # 2048 instances, G ~ U{2..12}, M ~ U{200..4000}, n_i ~ U{2..10}, k = 8:
+    # every right-hand side of every instance against the structured oracle
     probs = S.config2_instances(count=2048, k=8)
     bt, b, iters, relres, status = run_batch(probs, 8)
     st = np.array(status).reshape(2048, 8)
     assert np.all(np.isin(st, (0, 4))), np.unique(st)
     # columns that stopped at the float64 rounding floor stay near it
     assert np.max(np.concatenate([np.ravel(r) for r in relres])) <= 1e-10
-    for j in (0, 1, 777, 2047):
-        p = probs[j]
-        assert relcols(b[j], O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)) <= TOL_B, j
+    errs = np.array([relcols(b[j], O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)) for j, p in enumerate(probs)])
+    worst = int(np.argmax(errs))
+    assert errs[worst] <= TOL_B, (worst, errs[worst])

@@ -217,12 +217,13 @@ def test_restricted_iterations_match_reference_pcg():
     assert max(r["iters"]) <= p.m + 4 - p.n + 1
 
 
-def test_restricted_full_size_workload_sampled_columns():
+def test_restricted_full_size_workload_every_column():
     # G = 32, M = 50000, n_i = 16, C 64 x 512, k = 32: the restrictions hold
-    # for every column and two sampled columns match the structured oracle
+    # for every column and every column matches the structured oracle (one
+    # oracle call for all 32 right-hand sides: the QR of W is shared)
     p = S.config3(k=32)
     r = gpu_solve_restricted(p)
     assert np.max(np.linalg.norm(p.C @ r["b"] - p.d, axis=0) / np.linalg.norm(p.d, axis=0)) <= 1e-10
-    for j in (0, 31):
-        b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y[:, j:j + 1], p.C, p.d[:, j:j + 1])
-        assert relcols(r["b"][:, j:j + 1], b_ref) <= TOL_B, j
+    b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y, p.C, p.d)
+    errs = np.linalg.norm(r["b"] - b_ref, axis=0) / np.linalg.norm(b_ref, axis=0)
+    assert np.max(errs) <= TOL_B, (int(np.argmax(errs)), float(np.max(errs)), r["status"])
