@@ -23,175 +23,10 @@
 #include "common.cuh"
 #include "internal.h"
 #include "pcg.h"
+#include "pcg_dev.cuh"
 #include "tma.cuh"
 
 namespace glmsur {
-
-// ---------------------------------------------------------------------------
-// per-column scalar logic of the step prologue (identical in every CTA)
-// ---------------------------------------------------------------------------
-struct StepScalars {
-  double mu;
-  double lam_prev;
-  int act;
-  int act_prev;
-  int snap;   // save w of this step as the best iterate so far
-};
-
-__device__ StepScalars step_prologue(const PcgState& st, int j, int k, double csum, bool writer) {
-  StepScalars out{};
-  const int it = *st.it;
-  out.lam_prev = st.lam[j];
-  if (it == 0) {
-    const bool act = (csum > 0.0) && isfinite(csum);
-    out.act = act;
-    out.act_prev = 1;
-    out.mu = 0.0;
-    if (writer) {
-      st.c1[j] = csum;
-      st.c[0][j] = csum;
-      st.active[0][j] = act;
-      st.cbest[0][j] = csum;
-      st.itbest[0][j] = 0;
-      st.csnap[0][j] = csum;
-      st.cstop[j] = csum;
-      st.relres[j] = act ? 1.0 : 0.0;
-      st.status[j] = act ? kStatusRunning : (isfinite(csum) ? GLM_SUR_OK : GLM_SUR_NONFINITE);
-      st.iters[j] = 0;
-    }
-    return out;
-  }
-  const int sp = (it - 1) & 1, sc = it & 1;
-  const int ap = st.active[sp][j];
-  const double cp = st.c[sp][j];
-  out.act_prev = ap;
-  double cb = st.cbest[sp][j];
-  int ib = st.itbest[sp][j];
-  const double cs_prev = st.csnap[sp][j];
-  if (!ap) {
-    out.act = 0;
-    out.mu = 0.0;
-    if (writer) {
-      st.c[sc][j] = cp; st.active[sc][j] = 0; st.cbest[sc][j] = cb; st.itbest[sc][j] = ib;
-      st.csnap[sc][j] = cs_prev;
-    }
-    return out;
-  }
-  // the w formed in this step (lagged update) is saved when c dropped below
-  // a quarter of the c of the previous save
-  out.snap = isfinite(csum) && csum < 0.25 * cs_prev;
-  const double c1 = st.c1[j];
-  const double rr = sqrt(fmax(csum, 0.0) / c1);
-  int act = 1, status = kStatusRunning;
-  if (csum < cb) { cb = csum; ib = it; }
-  // stop tests: breakdown, convergence, stagnation (no new minimum of c for
-  // W steps: c need not decrease monotonically), iteration cap
-  if (!isfinite(csum) || csum < 0.0) { act = 0; status = GLM_SUR_BREAKDOWN; }
-  else if (rr <= st.tol) { act = 0; status = GLM_SUR_OK; }
-  else if (st.W > 0 && it - ib >= st.W) { act = 0; status = GLM_SUR_STAGNATED; }
-  else if (it >= st.maxit) { act = 0; status = GLM_SUR_NOT_CONVERGED; }
-  out.act = act;
-  out.mu = act ? csum / cp : 0.0;
-  if (writer) {
-    st.c[sc][j] = act ? csum : cp;
-    st.active[sc][j] = act;
-    st.cbest[sc][j] = cb;
-    st.itbest[sc][j] = ib;
-    st.csnap[sc][j] = out.snap ? csum : cs_prev;
-    st.cstop[j] = csum;
-    st.relres[j] = rr;
-    st.iters[j] = it;
-    if (!act) st.status[j] = status;
-  }
-  return out;
-}
-
-// Deterministic CTA reduction of per-thread partial sums, one per column
-// jj < JJ, where thread t holds column (t % JJ).  Result valid in threads
-// tid < JJ.  `red` needs (blockDim/32) * JJ doubles.
-template <int JJ>
-__device__ double reduce_cols_strided(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int off = 16; off >= JJ; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();
-  if (lane < JJ) red[warp * JJ + lane] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < JJ)
-    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
-  return s;
-}
-
-// Same reduction when every thread holds four columns, 4 (tid % (JJ/4)) + c
-// (c = 0..3).  Valid in threads tid < JJ.
-template <int JJ>
-__device__ double reduce_cols_quads(const double (&v)[4], double* red) {
-  constexpr int JQ = JJ / 4;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double x[4] = {v[0], v[1], v[2], v[3]};
-#pragma unroll
-  for (int off = 16; off >= JQ; off >>= 1)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] += __shfl_xor_sync(0xffffffffu, x[c], off);
-  __syncthreads();
-  if (lane < JQ)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) red[warp * JJ + 4 * lane + c] = x[c];
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < JJ)
-    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
-  return s;
-}
-
-// out[jj] = sum_{p < np} part[p*k + j0 + jj] for jj < JJ, using the whole CTA
-// (fixed order: deterministic).  Valid in threads tid < JJ.
-template <int JJ>
-__device__ double sum_partials(const double* __restrict__ part, int np, int k, int j0, double* red) {
-  const int jj = threadIdx.x % JJ, P = blockDim.x / JJ, q = threadIdx.x / JJ;
-  double v = 0.0;
-#pragma unroll 4
-  for (int p = q; p < np; p += P) v += part[(int64_t)p * k + j0 + jj];
-  return reduce_cols_strided<JJ>(v, red);
-}
-
-// Same for a runtime number of columns k <= blockDim: out[j] = sum_p part[p*k + j],
-// written to out_s[j] (shared).  Tree over a power-of-two number of slices.
-__device__ void sum_partials_cols(const double* __restrict__ part, int np, int k, double* red, double* out_s) {
-  int P = 1;
-  while (P * 2 * k <= (int)blockDim.x) P *= 2;
-  const int j = threadIdx.x % k, q = threadIdx.x / k;
-  double v = 0.0;
-  if (q < P)
-    for (int p = q; p < np; p += P) v += part[(int64_t)p * k + j];
-  __syncthreads();
-  if (q < P) red[q * k + j] = v;
-  __syncthreads();
-  for (int h = P / 2; h >= 1; h >>= 1) {
-    if (q < h) red[q * k + j] += red[(q + h) * k + j];
-    __syncthreads();
-  }
-  if (threadIdx.x < k) out_s[threadIdx.x] = red[threadIdx.x];
-  __syncthreads();
-}
-
-// Every thread holds JJ partial sums (one per column); result in tid < JJ.
-template <int JJ>
-__device__ double reduce_cols_all(const double (&v)[JJ], double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-#pragma unroll
-  for (int jj = 0; jj < JJ; ++jj) {
-    const double s = warp_sum(v[jj]);
-    if (lane == 0) red[warp * JJ + jj] = s;
-  }
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < JJ)
-    for (int w = 0; w < nw; ++w) s += red[w * JJ + threadIdx.x];
-  return s;
-}
 
 // ---------------------------------------------------------------------------
 // sigma_step: prologue, lagged w update, u update, S = U Omega, d partials.
@@ -535,10 +370,12 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
     }
   }
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
-    T cs = 0;
+  // g^T g: per-tile partial sums in the working precision, added in float64
+  double csd = 0.0;
   __syncthreads();
   for (int64_t t0 = r0; t0 < r1; t0 += TRB) {
     const int tr = (int)((r1 - t0) < (int64_t)TRB ? (r1 - t0) : (int64_t)TRB);
+    T cs = 0;
     if (tid < nqg) {
       const T* qp = Q + t0 * np + 4 * (q0 + tid);
       for (int r = 0; r < tr; r += 2) {
@@ -592,9 +429,10 @@ k_proj_update(int64_t M, int G, int np, int k, int TRB, const T* __restrict__ Q,
         }
       }
     }
+    csd += (double)cs;
     __syncthreads();
   }
-  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  const double tot = reduce_cols_strided<JJ>(csd, red);
   if (tid < JJ) cpart[cp_idx + tid] = tot;
 }
 
@@ -788,7 +626,7 @@ k_proj_update_tma(int64_t M, int G, int np, int nq, int TRB, int NST, const T* _
   };
   if (tid == 0)
     for (; issued < NST && issued < ntiles; ++issued) issue(issued);
-  T cs = 0;
+  double csd = 0.0;   // g^T g: per-tile partial sums in T, added in float64
   for (int tile = 0; tile < ntiles; ++tile) {
     const int sidx = tile % NST;
     if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
@@ -805,6 +643,7 @@ k_proj_update_tma(int64_t M, int G, int np, int nq, int TRB, int NST, const T* _
     const T* Qs = stage0 + sidx * stage_elems;
     const T* Ss = Qs + (int64_t)TRB * np;
     const T* gs = Ss + (int64_t)TRB * GK;
+    T cs = 0;
     // part[(r*JJ + jj)*nqp + q]: consecutive threads write consecutive words,
     // and the readers below (consecutive jj) hit distinct banks (nqp % 32 == 1)
     if (tid < nq) {
@@ -834,10 +673,11 @@ k_proj_update_tma(int64_t M, int G, int np, int nq, int TRB, int NST, const T* _
       g[row0 * GK + o] = gn;
       cs += gn * gn;
     }
+    csd += (double)cs;
     __syncthreads();
     if (tid == 0 && issued < ntiles) issue(issued++);
   }
-  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  const double tot = reduce_cols_strided<JJ>(csd, red);
   if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
 }
 
@@ -921,7 +761,7 @@ k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict
   };
   if (tid == 0)
     for (; issued < NST && issued < ntiles; ++issued) issue(issued);
-  T cs = 0;
+  double csd = 0.0;   // g^T g: per-tile partial sums in T, added in float64
   for (int tile = 0; tile < ntiles; ++tile) {
     const int sidx = tile % NST;
     if (tid == 0 && !mbar_wait_bounded(&full[sidx], (tile / NST) & 1, kWaitLimitNs)) {
@@ -938,6 +778,7 @@ k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict
     const T* Qs = stage0 + sidx * stage_elems;
     const T* Ss = Qs + (int64_t)TRB * np;
     const T* gs = Ss + (int64_t)TRB * GK;
+    T cs = 0;
     for (int r = rg; r < tr; r += nrg) {
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
@@ -961,12 +802,13 @@ k_proj_update_bj(int64_t M, int G, int np, int TRB, int NST, const T* __restrict
         }
       }
     }
+    csd += (double)cs;
     __syncthreads();
     if (tid == 0 && issued < ntiles) issue(issued++);
   }
   // per-column sums: thread's columns are jjp[a]; with npairs a multiple of JJ
   // and blockDim a multiple of JJ every thread's jj is tid % JJ
-  const double tot = reduce_cols_strided<JJ>((double)cs, red);
+  const double tot = reduce_cols_strided<JJ>(csd, red);
   if (tid < JJ) cpart[(int64_t)blockIdx.x * JJ + tid] = tot;
 }
 
