@@ -163,7 +163,8 @@ def aggregate(ms_local, pg, world, device="cpu"):
     return ms, world * 1e3 / ms
 
 
-NCU_SECTION = {"sigma_step": "k_sigma_step_tma", "proj_partial": "k_proj_partial_tma", "proj_update": "k_proj_update_bj"}
+NCU_SECTION = {"sigma_step": "k_sigma_step_tma", "proj_partial": "k_proj_partial_tma", "proj_update": "k_proj_update_bj",
+               "pass_a": "k_tc_pass_a", "pass_b": "k_tc_pass_b"}
 
 
 def ncu_traffic(args, kernel):
@@ -297,13 +298,21 @@ def run_ours(args, rank, world, local, pg):
     pb = 4 if args.precision == "fp32_refine" else 8
     M, G = args.M, args.G
     mk = m * k
-    kbytes = {   # algorithmic bytes per launch of each kernel of a step
-        "sigma_step": 6 * pb * mk,                 # read g, u, w; write u, w, S
-        "proj_partial": pb * M * n + pb * mk,      # read Q, S
-        "reduce": 0,
-        "proj_update": pb * M * n + 3 * pb * mk,   # read Q, S, g; write g
-    }
-    names = ["sigma_step", "proj_partial", "reduce", "proj_update"]
+    step_path = L.glm_sur_step_path(h.handle)
+    if step_path == 1:
+        # fused two-pass step, Sigma-apply on the tensor cores (S never stored)
+        kbytes = {"pass_a": pb * M * n + 3 * pb * mk,    # read Q, g, u; write u
+                  "-": 0, "reduce": 0,
+                  "pass_b": pb * M * n + 5 * pb * mk}    # read Q, u, g, w; write g, w
+        names = ["pass_a", "-", "reduce", "pass_b"]
+    else:
+        kbytes = {   # algorithmic bytes per launch of each kernel of a step
+            "sigma_step": 6 * pb * mk,                 # read g, u, w; write u, w, S
+            "proj_partial": pb * M * n + pb * mk,      # read Q, S
+            "reduce": 0,
+            "proj_update": pb * M * n + 3 * pb * mk,   # read Q, S, g; write g
+        }
+        names = ["sigma_step", "proj_partial", "reduce", "proj_update"]
     dom = max(range(4), key=lambda i: prof[i])
     dname = names[dom]
     ach = kbytes[dname] / (prof[dom] * 1e-3) / 1e9
@@ -388,7 +397,8 @@ def run_ours(args, rank, world, local, pg):
                          "algorithmic_bytes": kbytes[dname], "ms": prof[dom]},
             "roofline_iter": {"bound": "hbm", "achieved": ach_iter, "peak": hbm, "unit": "GB/s",
                               "frac": ach_iter / hbm, "B_iter": b_iter, "ms": prof[4],
-                              "kernel_ms": dict(zip(names, prof[:4]))},
+                              "kernel_ms": {nm: t for nm, t in zip(names, prof[:4]) if nm != "-"},
+                              "step_kernels": "tensor-core fused two-pass" if step_path == 1 else "simt four-launch"},
             "fp64_pcg": fp64,
             "row_reduced": reduced,
             "cpu_baseline": cpu,

@@ -76,10 +76,20 @@ typedef struct {
                              rem:reduction (M' = n rows), when M >= 2 n,
                              n <= 2048 and W = [X_1 ... X_G] has full column
                              rank (otherwise the model is kept whole)         */
+  int step_kernels;       /* GLM_SUR_STEP_*: kernels of the float32 bulk steps   */
 } glm_sur_opts;
 
+enum {
+  GLM_SUR_STEP_AUTO = 0,  /* fused two-pass step with the Sigma-apply on the
+                             tensor cores (tcgen05, three tf32 products) when
+                             k is 8 or 16, G <= 64, n_i <= 32 and
+                             sum_i 4 ceil(n_i / 4) <= 2048; otherwise SIMT */
+  GLM_SUR_STEP_SIMT = 1   /* four launches per step, Sigma-apply on the FP32
+                             FMA pipe                                        */
+};
+
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
- * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0.  A column that stops without
+ * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0, step_kernels AUTO.  A column that stops without
  * converging (stagnation, breakdown, maxit) returns its best saved iterate:
  * w is saved whenever c falls below a quarter of the c of the previous save. */
 void glm_sur_default_opts(glm_sur_opts* opts);
@@ -209,6 +219,11 @@ glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream
  * Either pointer may be NULL.  GLM_SUR_INVALID_ARG on a handle set up with
  * reduce_rows (its factors are those of the reduced model). */
 glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* R, glm_sur_stream_t stream);
+
+/* Kernels of the PCG steps of the last solve: 1 = fused two-pass float32
+ * step with the Sigma-apply on the tensor cores, 0 = four launches per step
+ * on the SIMT pipes, -1 = no solve yet.  Host-side query. */
+int glm_sur_step_path(glm_sur_t h);
 
 /* Number of kernel launches (including the nodes of replayed CUDA graphs)
  * this handle has issued since glm_sur_setup.  Host-side counter. */

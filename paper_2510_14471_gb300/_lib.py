@@ -30,12 +30,15 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "rank_deficient", 3: "breakdown", 
 GLM_SUR_PREC_FP64 = 0
 GLM_SUR_PREC_FP32_REFINE = 1
 
+GLM_SUR_STEP_AUTO = 0
+GLM_SUR_STEP_SIMT = 1
+
 
 class GlmSurOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("stagnation_window", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("chunk", ctypes.c_int), ("inner_shift", ctypes.c_double),
-                ("reduce_rows", ctypes.c_int)]
+                ("reduce_rows", ctypes.c_int), ("step_kernels", ctypes.c_int)]
 
 
 # (name, restype, argtypes) of every exported entry point
@@ -56,6 +59,7 @@ SIGNATURES = {
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
     "glm_sur_destroy": (None, [_VP]),
     "glm_sur_launch_count": (ctypes.c_int64, [_VP]),
+    "glm_sur_step_path": (_I, [_VP]),
     "glm_sur_ols_static": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP]),
     "glm_sur_profile_steps": (_I, [_VP, _I, ctypes.POINTER(_D), _VP]),
     "glm_sur_batch_setup": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -168,6 +172,10 @@ def glm_sur_get_factors(h: int, Q_ptr: int, ldq: int, R_ptr: int, stream: int) -
 
 def glm_sur_launch_count(h: int) -> int:
     return int(lib().glm_sur_launch_count(h))
+
+
+def glm_sur_step_path(h: int) -> int:
+    return int(lib().glm_sur_step_path(h))
 
 
 def glm_sur_profile_steps(h: int, reps: int, stream: int):

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -137,6 +138,7 @@ glm_sur_status validate_opts(const glm_sur_opts* o) {
   if (!(o->tol >= 0.0) || !(o->inner_tol > 0.0)) return GLM_SUR_INVALID_ARG;
   if (o->chunk < 2 || (o->chunk & 1)) return GLM_SUR_INVALID_ARG;
   if (!(o->inner_shift >= 0.0) || o->inner_shift > 1e-2) return GLM_SUR_INVALID_ARG;
+  if (o->step_kernels != GLM_SUR_STEP_AUTO && o->step_kernels != GLM_SUR_STEP_SIMT) return GLM_SUR_INVALID_ARG;
   return GLM_SUR_OK;
 }
 
@@ -175,6 +177,8 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
   // TMA-streamed step kernels: one CTA per SM, whole rows (all k) per tile
   const size_t GK_bytes = sz * (size_t)gm.G * k;
   const size_t budget_tma = 200 * 1024;
+  int nmax = 0;
+  for (int v : h->n_i) nmax = std::max(nmax, v);
   if (p.JJ == k && GK_bytes % 16 == 0) {
     // Sigma step: items are (RI-row group, column quad of Omega, rhs); pick RI
     // and the tile height TR so that a tile holds >= 512 items when shared
@@ -211,8 +215,6 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
       }
     }
     // block x column update: every block at most 32 columns, G*k pairs on <= 2 per thread
-    int nmax = 0;
-    for (int v : h->n_i) nmax = std::max(nmax, v);
     const int npairs = gm.G * k;
     if (nmax <= 32 && npairs <= 1024 && (!is_double || npairs <= 512)) {
       p.bj_np = npairs > 512 ? 2 : 1;
@@ -246,6 +248,57 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
       p.n_cpart = h->sms;
     }
     p.extra_cpart = h->kc > 0 ? 1 : 0;
+    // fused float32 step with the tensor-core Sigma-apply (pcg_tc.cu)
+    if (!is_double && h->kc == 0 && h->opts.step_kernels != GLM_SUR_STEP_SIMT &&
+        tc_step_eligible(gm.G, k, gm.np, nmax)) {
+      p.tc_gp = gm.G <= 32 ? 32 : 64;
+      const int TV = 128 / k;
+      const size_t tc_budget = 224 * 1024;
+      // Q ring of each pass: the largest number of rows in flight (tq x nsq,
+      // nsq >= 2) that fits next to the fixed buffers; pass B keeps two g tiles
+      // in flight when it can
+      auto pick_q = [&](int pass, int nsg, int& tq_out, int& nsq_out) {
+        int best = 0;
+        for (int tq = TV; tq >= 1; tq >>= 1)
+          for (int nsq = 2; nsq <= 4; ++nsq) {
+            const TcSmem L = tc_smem_layout(pass, gm.G, p.tc_gp, k, gm.np, tq, nsq, nsg);
+            if (L.total <= tc_budget && tq * nsq > best) {
+              best = tq * nsq;
+              tq_out = tq;
+              nsq_out = nsq;
+            }
+          }
+        return best > 0;
+      };
+      bool ok = pick_q(0, 0, p.tc_tq_a, p.tc_nsq_a);
+      // pass B: two g tiles in flight when the Q ring still holds two full
+      // vector tiles of rows, else one
+      int tq2 = 0, nsq2 = 0, tq1 = 0, nsq1 = 0;
+      const bool ok2 = pick_q(1, 2, tq2, nsq2), ok1 = pick_q(1, 1, tq1, nsq1);
+      const bool okb = ok2 || ok1;
+      if (ok2 && (tq2 * nsq2 >= 2 * TV || !ok1)) {
+        p.tc_nsg = 2; p.tc_tq_b = tq2; p.tc_nsq_b = nsq2;
+      } else if (ok1) {
+        p.tc_nsg = 1; p.tc_tq_b = tq1; p.tc_nsq_b = nsq1;
+      }
+      if (const char* env = getenv("GLMSUR_TC_RING")) {   // tuning override: "tqa,nsqa,tqb,nsqb,nsg"
+        int a0, a1, b0, b1, b2;
+        if (sscanf(env, "%d,%d,%d,%d,%d", &a0, &a1, &b0, &b1, &b2) == 5 && a0 >= 1 && TV % a0 == 0 &&
+            b0 >= 1 && TV % b0 == 0 && a1 >= 1 && b1 >= 1 && b2 >= 1 && a1 + 2 <= 16 && b1 + b2 + 2 <= 16 &&
+            tc_smem_layout(0, gm.G, p.tc_gp, k, gm.np, a0, a1, 0).total <= tc_budget &&
+            tc_smem_layout(1, gm.G, p.tc_gp, k, gm.np, b0, b1, b2).total <= tc_budget) {
+          p.tc_tq_a = a0; p.tc_nsq_a = a1; p.tc_tq_b = b0; p.tc_nsq_b = b1; p.tc_nsg = b2;
+        }
+      }
+      if (ok && okb) {
+        p.tc_a_smem = tc_smem_layout(0, gm.G, p.tc_gp, k, gm.np, p.tc_tq_a, p.tc_nsq_a, 0).total;
+        p.tc_b_smem = tc_smem_layout(1, gm.G, p.tc_gp, k, gm.np, p.tc_tq_b, p.tc_nsq_b, p.tc_nsg).total;
+        p.tc_step = true;
+        p.launches_per_step = 3;
+        p.n_sigma = p.n_partial_rows = p.n_update = p.n_cpart = h->sms;
+        p.n_qgroups = 1;
+      }
+    }
   }
   cudaError_t e = is_double ? set_smem_attrs<double>(p.JJ, p.sigma_smem, p.update_smem)
                             : set_smem_attrs<float>(p.JJ, p.sigma_smem, p.update_smem);
@@ -258,6 +311,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
                                               std::max<size_t>(p.update_tma_smem, 1024),
                                               std::max<size_t>(p.bj_smem, 1024),
                                               std::max<size_t>(p.partial_tma_smem, 1024));
+  if (e == cudaSuccess && p.tc_step) e = tc_prepare(k, p.tc_gp, p.tc_a_smem, p.tc_b_smem);
   if (e != cudaSuccess) {
     set_last_error(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
     return GLM_SUR_CUDA_ERROR;
@@ -385,6 +439,16 @@ void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
   T* Cpart = reinterpret_cast<T*>(h->Cpart);
   T* C = reinterpret_cast<T*>(h->Cfin);
   for (int i = 0; i < n; ++i) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      if (p.tc_step) {
+        // pass A (u, S = U Omega on the tensor cores, d and C partials), reduce, pass B
+        launch_tc_pass_a(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, h->wb32, h->st, h->cpart,
+                         p.n_cpart + p.extra_cpart, h->dpart, Cpart, s);
+        launch_reduce<float>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
+        launch_tc_pass_b(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, C, h->st, h->cpart, s);
+        continue;
+      }
+    }
     launch_sigma_step<T>(p, h->gm, k, Bufs<T>::Om(h), Bufs<T>::g(h), Bufs<T>::u(h), Bufs<T>::w(h), Bufs<T>::S(h),
                          Bufs<T>::wb(h), h->st, h->cpart, h->dpart, s);
     launch_proj_partial<T>(p, h->gm, k, Bufs<T>::Q(h), Bufs<T>::S(h), Cpart, h->st, 1, s);
@@ -427,7 +491,7 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
   const int64_t max_launch = (int64_t)maxit / chunk + 3;
   for (int64_t c = 0; c < max_launch; ++c) {
     GS_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
-    h->launches += (h->kc > 0 ? 6 : 4) * (int64_t)chunk;
+    h->launches += (h->kc > 0 ? 6 : h->plan.launches_per_step) * (int64_t)chunk;
     // done flag and error word side by side: h_done[2*slot], h_done[2*slot + 1]
     GS_CUDA_TRY(cudaMemcpyAsync(&h->h_done[2 * (c & 1)], h->st.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA_TRY(cudaEventRecord(h->ev[c & 1], s));
@@ -637,6 +701,7 @@ void glm_sur_default_opts(glm_sur_opts* o) {
   o->chunk = 16;
   o->inner_shift = 0.0;
   o->reduce_rows = 0;
+  o->step_kernels = GLM_SUR_STEP_AUTO;
 }
 
 const char* glm_sur_status_string(glm_sur_status s) {
@@ -1182,6 +1247,12 @@ glm_sur_status glm_sur_get_factors(glm_sur_t h, double* Q, int64_t ldq, double* 
   return GLM_SUR_OK;
 }
 
+int glm_sur_step_path(glm_sur_t h) {
+  if (h && h->sub) return glm_sur_step_path(h->sub);
+  if (!h || h->plan_k < 1) return -1;
+  return h->plan.tc_step ? 1 : 0;
+}
+
 int64_t glm_sur_launch_count(glm_sur_t h) {
   if (!h) return -1;
   return h->launches + (h->sub ? glm_sur_launch_count(h->sub) : 0);
@@ -1217,17 +1288,29 @@ glm_sur_status glm_sur_profile_steps(glm_sur_t h, int reps, double* ms, glm_sur_
     } else {
       float* Cp = reinterpret_cast<float*>(h->Cpart);
       float* C = reinterpret_cast<float*>(h->Cfin);
-      launch_sigma_step<float>(p, h->gm, k, h->Om32, h->g32, h->u32, h->w32, h->S32, h->wb32, h->st, h->cpart,
-                               h->dpart, s);
-      if (timed) cudaEventRecord(ev[1], s);
-      launch_proj_partial<float>(p, h->gm, k, h->Q32, h->S32, Cp, h->st, 1, s);
-      if (timed) cudaEventRecord(ev[2], s);
-      launch_reduce<float>(p, h->gm, k, Cp, C, h->st, 1, h->dpart, s);
-      if (timed) cudaEventRecord(ev[3], s);
-      launch_proj_update<float>(p, h->gm, k, h->Q32, h->S32, h->g32, C, 1, h->st.lam, 0.0, h->cpart, h->st, 1, s);
+      if (p.tc_step) {
+        // ms[0] pass A, ms[1] 0 (its projection partials are inside pass A), ms[2] reduce, ms[3] pass B
+        launch_tc_pass_a(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, h->wb32, h->st, h->cpart,
+                         p.n_cpart + p.extra_cpart, h->dpart, Cp, s);
+        if (timed) cudaEventRecord(ev[1], s);
+        if (timed) cudaEventRecord(ev[2], s);
+        launch_reduce<float>(p, h->gm, k, Cp, C, h->st, 1, h->dpart, s);
+        if (timed) cudaEventRecord(ev[3], s);
+        launch_tc_pass_b(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, C, h->st, h->cpart, s);
+      } else {
+        launch_sigma_step<float>(p, h->gm, k, h->Om32, h->g32, h->u32, h->w32, h->S32, h->wb32, h->st, h->cpart,
+                                 h->dpart, s);
+        if (timed) cudaEventRecord(ev[1], s);
+        launch_proj_partial<float>(p, h->gm, k, h->Q32, h->S32, Cp, h->st, 1, s);
+        if (timed) cudaEventRecord(ev[2], s);
+        launch_reduce<float>(p, h->gm, k, Cp, C, h->st, 1, h->dpart, s);
+        if (timed) cudaEventRecord(ev[3], s);
+        launch_proj_update<float>(p, h->gm, k, h->Q32, h->S32, h->g32, C, 1, h->st.lam, 0.0, h->cpart, h->st, 1,
+                                  s);
+      }
     }
     if (timed) cudaEventRecord(ev[4], s);
-    h->launches += 4;
+    h->launches += p.launches_per_step;
   };
   for (int r = 0; r < 3; ++r) one(false);
   for (int r = 0; r < reps; ++r) {

@@ -36,7 +36,46 @@ struct IterPlan {
   bool tma_partial = false;  // TMA-streamed projection partials (n' / 4 <= 512 quads)
   int tr_partial = 1, nst_partial = 3, partial_threads = 64;
   size_t partial_tma_smem = 0;
+  // fused float32 step with the Sigma-apply on the tensor cores (pcg_tc.cu):
+  // pass A, reduce, pass B; Gp = G padded to 32 or 64; Q sub-tiles of tc_tq_*
+  // rows in rings of tc_nsq_* stages; tc_nsg staged g tiles in pass B
+  bool tc_step = false;
+  int tc_gp = 64, tc_tq_a = 4, tc_nsq_a = 2, tc_tq_b = 2, tc_nsq_b = 2, tc_nsg = 2;
+  size_t tc_a_smem = 0, tc_b_smem = 0;
+  int launches_per_step = 4;
 };
+
+// Shared-memory layout of the tensor-core step kernels (byte offsets); pass 0
+// stages g and u tiles and keeps the S tile, pass 1 stages one u tile and NSG
+// g tiles and keeps the (Q C) tile.  The U operand of the MMA and the
+// accumulator live in tensor memory.
+struct TcSmem {
+  uint32_t om, vec, tile, q, total;
+};
+__host__ __device__ inline TcSmem tc_smem_layout(int pass, int G, int Gp, int KK, int np, int TQ, int NSQ, int NSG) {
+  TcSmem L;
+  const uint32_t TV = 128u / (uint32_t)KK;
+  const uint32_t tile_bytes = TV * (uint32_t)G * KK * 4u;
+  uint32_t off = 128;   // mbarriers (at most 16)
+  L.om = off;
+  off += 2u * Gp * Gp * 4u;
+  L.vec = off;
+  off += (pass == 0 ? 2u : 1u + (uint32_t)NSG) * tile_bytes;
+  L.tile = off;
+  off += tile_bytes;
+  L.q = off;
+  off += (uint32_t)NSQ * TQ * (uint32_t)np * 4u;
+  L.total = off;
+  return L;
+}
+
+bool tc_step_eligible(int G, int k, int np, int nmax_cols);
+cudaError_t tc_prepare(int k, int Gp, size_t a_bytes, size_t b_bytes);
+void launch_tc_pass_a(const IterPlan& p, const Geom& gm, int k, const float* Om, const float* Q, const float* g,
+                      float* u, const float* w, float* wbest, const PcgState& st, const double* cpart, int ncpart,
+                      double* dpart, float* Cpart, cudaStream_t s);
+void launch_tc_pass_b(const IterPlan& p, const Geom& gm, int k, const float* Om, const float* Q, float* g,
+                      const float* u, float* w, const float* C, const PcgState& st, double* cpart, cudaStream_t s);
 
 template <typename T>
 void launch_sigma_step(const IterPlan& p, const Geom& gm, int k, const T* Om, T* g, T* u, T* w, T* S, T* wbest,

@@ -40,6 +40,7 @@ def main(argv=None):
     ap.add_argument("--rank", type=int, default=56)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--Mmax", type=int, default=4000)
+    ap.add_argument("--step-kernels", default="auto", choices=["auto", "simt"])
     a = ap.parse_args(argv)
     if a.batch:
         return profile_batch(a)
@@ -49,14 +50,19 @@ def main(argv=None):
     from paper_2510_14471_gb300.sur import GlmSur
 
     p = S.config1(k=a.k, M=a.M, G=a.G, rank=min(a.rank, a.G), nmin=a.nmin, nmax=a.nmax)
-    h = GlmSur(p.X_blocks, p.Omega, precision=a.precision, maxit=2, max_refine=1)
+    h = GlmSur(p.X_blocks, p.Omega, precision=a.precision, maxit=2, max_refine=1, step_kernels=a.step_kernels)
     h.solve(p.Y)
     torch.cuda.synchronize()
     ms = L.glm_sur_profile_steps(h.handle, a.reps, torch.cuda.current_stream().cuda_stream)
     pb = 4 if a.precision == "fp32_refine" else 8
     mk, Mn = p.m * p.k, p.M * p.n
-    names = ["sigma_step", "proj_partial", "reduce", "proj_update", "step"]
-    alg = [6 * pb * mk, pb * (Mn + mk), 0, pb * (Mn + 3 * mk), 2 * pb * Mn + 8 * pb * mk]
+    if L.glm_sur_step_path(h.handle) == 1:
+        # fused two-pass step, Sigma-apply on the tensor cores
+        names = ["pass_a", "-", "reduce", "pass_b", "step"]
+        alg = [pb * (Mn + 3 * mk), 0, 0, pb * (Mn + 5 * mk), 2 * pb * Mn + 8 * pb * mk]
+    else:
+        names = ["sigma_step", "proj_partial", "reduce", "proj_update", "step"]
+        alg = [6 * pb * mk, pb * (Mn + mk), 0, pb * (Mn + 3 * mk), 2 * pb * Mn + 8 * pb * mk]
     out = {"workload": f"sur-singular-g{a.G}-m{a.M}-k{a.k}", "precision": a.precision,
            "ms": dict(zip(names, ms)), "algorithmic_bytes": dict(zip(names, alg)),
            "GBps": {nm: (b / (t * 1e-3) / 1e9 if t > 0 else None) for nm, b, t in zip(names, alg, ms)}}
