@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-reduced", action="store_true", help="skip the row-reduced comparison solve")
     ap.add_argument("--profile-reps", type=int, default=20)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched, constrained and differentiable summaries")
     ap.add_argument("--workload", default="singular", choices=["singular", "batched", "constrained", "differentiable"],
                     help="singular: the headline workload; the others measure the batched, restricted and "
                          "adjoint paths on their own workloads")
@@ -182,6 +184,38 @@ def ncu_traffic(args, kernel):
         elif line.startswith("traffic_bytes_per_launch:") and cur == NCU_SECTION[kernel]:
             return int(line.split(":")[1])
     return None
+
+
+EXTRA_WORKLOADS = ("batched", "constrained", "differentiable")
+
+
+def run_extras(timeout_s=420):
+    """The other workloads, each run once (one warm-up, one timed solve) in a
+    child process of this script; returns a summary of each one's JSON line."""
+    import subprocess
+    out = {}
+    for w in EXTRA_WORKLOADS:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", w, "--steps", "1", "--warmup", "1",
+               "--no-cpu", "--no-reduced"]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+            line = None
+            for ln in r.stdout.splitlines():
+                if ln.startswith("{"):
+                    line = json.loads(ln)
+            if r.returncode != 0 or line is None:
+                out[w] = {"error": f"rc={r.returncode}: {r.stderr.strip().splitlines()[-1:] if r.stderr else ''}"}
+                continue
+        except subprocess.TimeoutExpired:
+            out[w] = {"error": f"did not finish within {timeout_s} s"}
+            continue
+        keep = ["value", "unit", "ms_per_step", "dtype", "config", "roofline", "roofline_iter", "e2e", "gpu_launches",
+                "clocks", "rel_err_sampled", "rel_err", "status_counts", "steps_per_instance", "iters_max", "k1",
+                "grad_err", "b_err", "steps"]
+        out[w] = {k2: line[k2] for k2 in keep if k2 in line}
+        out[w]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(args, rank, world, pg):
@@ -365,6 +399,20 @@ def run_ours(args, rank, world, local, pg):
                                            "one float64 product Q^T Y per solve"}
         hr.close()
 
+    # ---- the float32 bulk alone: one float32 PCG run to its own floor, no
+    # float64 refinement step after it (the "unrefined" error)
+    unrefined = None
+    if args.precision == "fp32_refine":
+        hu = GlmSur(p.X_blocks, p.Omega, precision="fp32_refine", tol=1e-13, inner_tol=1e-13, max_refine=1,
+                    device=dev)
+        L.glm_sur_solve(hu.handle, Ycm.data_ptr(), m, k, b.data_ptr(), n, iters.data_ptr(), relres.data_ptr(), stream)
+        torch.cuda.synchronize()
+        unrefined = {"rel_err_vs_beta_true": rel_err(b.t().cpu().numpy(), p.beta),
+                     "iters_max": int(iters.cpu().numpy().max()),
+                     "note": "one float32 PCG run (inner tolerance 1e-13, stops at its float32 floor), "
+                             "correction projected in float64, no refinement step"}
+        hu.close()
+
     # ---- CPU oracle baseline (rank 0, bounded sample)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -379,6 +427,15 @@ def run_ours(args, rank, world, local, pg):
                "sample": f"{n_iter} steps of the float64 reference PCG (numpy, k={k}) timed, "
                          f"x {iters_ref} steps per solve ({src}); setup QR excluded",
                "sec_per_step": t_iter}
+        # the oracle's structured direct GLS (Remark rem:reduction + eigen-split of
+        # Omega), timed on the whole workload: a measurement, not a projection
+        from oracle import sur_oracle as O
+        t0 = time.perf_counter()
+        b_o2 = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)
+        t_o2 = time.perf_counter() - t0
+        cpu["direct_structured"] = {"seconds": t_o2, "solves_per_s": 1.0 / t_o2,
+                                    "rel_err_vs_beta_true": rel_err(b_o2, p.beta),
+                                    "sample": f"one full solve, all k={k} right-hand sides"}
 
     if rank == 0:
         line = {
@@ -401,14 +458,21 @@ def run_ours(args, rank, world, local, pg):
                               "step_kernels": "tensor-core fused two-pass" if step_path == 1 else "simt four-launch"},
             "fp64_pcg": fp64,
             "row_reduced": reduced,
+            "unrefined": unrefined,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_sps, "unit": "solves/s", "h2d_bytes_per_step": int(m * k * 8),
                     "d2h_bytes_per_step": int(n * k * 8), "rel_err_max": e2e_err},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        if world == 1 and not args.no_extras:
+            h.close()
+            h = None
+            torch.cuda.empty_cache()
+            line["workloads"] = run_extras()
         print(json.dumps(line))
-    h.close()
+    if h is not None:
+        h.close()
     return 0
 
 

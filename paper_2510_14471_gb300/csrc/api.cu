@@ -271,12 +271,12 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
         return best > 0;
       };
       bool ok = pick_q(0, 0, p.tc_tq_a, p.tc_nsq_a);
-      // pass B: two g tiles in flight when the Q ring still holds two full
-      // vector tiles of rows, else one
+      // pass B: two g tiles in flight when the Q ring still holds a full
+      // vector tile of rows, else one
       int tq2 = 0, nsq2 = 0, tq1 = 0, nsq1 = 0;
       const bool ok2 = pick_q(1, 2, tq2, nsq2), ok1 = pick_q(1, 1, tq1, nsq1);
       const bool okb = ok2 || ok1;
-      if (ok2 && (tq2 * nsq2 >= 2 * TV || !ok1)) {
+      if (ok2 && (tq2 * nsq2 >= TV || !ok1)) {
         p.tc_nsg = 2; p.tc_tq_b = tq2; p.tc_nsq_b = nsq2;
       } else if (ok1) {
         p.tc_nsg = 1; p.tc_tq_b = tq1; p.tc_nsq_b = nsq1;

@@ -21,16 +21,23 @@
 // B[h][g] = Om[g][h] (Gp = G padded to 32 or 64), issued as tcgen05.mma
 // kind::tf32: A in tensor memory, B in shared memory, the accumulator in
 // tensor memory.  float32 accuracy comes from splitting both operands into
-// tf32 high and low parts and summing three products, A_hi B_hi + A_hi B_lo
-// + A_lo B_hi (the dropped A_lo B_lo term is of relative size 2^-22).
+// tf32 high and low parts (hi = x with the low 13 mantissa bits cleared,
+// lo = x - hi exactly) and summing three products, A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (the dropped A_lo B_lo term is of relative size 2^-20).  Per
+// eight values of K one MMA of N = 2 Gp multiplies A_hi by [B_hi; B_lo]
+// (columns 0 .. Gp - 1 and Gp .. 2 Gp - 1 of the accumulator) and one of
+// N = Gp adds A_lo B_hi to the first half; S is the sum of the two halves.
 // Thread (warp w, lane l) owns MMA row r = 32 (w % 4) + l (its quarter of the
 // tensor-memory lanes) and the HB columns h = HB (w / 4) ...: it stores
 // exactly the operand entries whose products it reads back, so u and S never
-// change hands between threads.  Tensor-memory columns: D at 0, A_hi at 64,
-// A_lo at 128; pass B keeps the C values of its (block, rhs) pairs at 256 ...
+// change hands between threads.  Tensor-memory columns: accumulator at 0
+// (2 Gp), A_hi at 128, A_lo at 192; pass B keeps the C values of its (block,
+// rhs) pairs at 256 ...
 //
-// Overlap.  Pass A issues the MMA of tile i and projects tile i - 1 while it
-// runs; pass B forms (Q C) of tile i while the MMA of tile i runs.
+// Overlap.  Pass A issues the MMA of tile i, writes the updated u tile back
+// by a bulk copy and refills the stage from a warp without projection work,
+// and projects tile i - 1 meanwhile; pass B forms (Q C) of tile i while the
+// MMA of tile i runs.
 //
 // Memory: vector row tiles (contiguous in the (M, G, k) layout) and Q row
 // sub-tiles of TQ rows are brought into shared memory by 1-D bulk copies
@@ -53,50 +60,67 @@ namespace {
 constexpr int kTcThreads = 512;
 constexpr int kTcRows = 128;   // MMA rows (t, j) per tile
 // tensor-memory columns: accumulator, A operand (tf32 high, low parts), C of pass B
-constexpr uint32_t kColAhi = 64, kColAlo = 128, kColC = 256;
+constexpr uint32_t kColAhi = 128, kColAlo = 192, kColC = 256;
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ void st_smem_f(float* base, uint32_t byte_off, float v) {
   *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(base) + byte_off) = v;
 }
 
 // Omega as the B operand, split into tf32 high and low parts:
-// B[h][g] = Om[g][h] for g, h < G, zero in the padding.
+// B[h][g] = Om[g][h] for g, h < G, zero in the padding; the low parts are the
+// rows Gp .. 2 Gp - 1 of the same K-major operand.
 template <int Gp>
-__device__ void load_omega_split(const float* __restrict__ Om, int G, int Gq, float* Bhi, float* Blo) {
+__device__ void load_omega_split(const float* __restrict__ Om, int G, int Gq, float* Bhi) {
+  float* Blo = Bhi + Gp * Gp;
   for (int e = threadIdx.x; e < Gp * Gp; e += blockDim.x) {
     const int h = e / Gp, gg = e % Gp;
     const float v = (h < G && gg < G) ? Om[(int64_t)gg * Gq + h] : 0.f;
-    const float hi = to_tf32(v);
+    const float hi = tf32_trunc(v);
     const uint32_t off = kmajor_offset(h, gg, Gp);
     st_smem_f(Bhi, off, hi);
-    st_smem_f(Blo, off, to_tf32(v - hi));
+    st_smem_f(Blo, off, v - hi);
   }
 }
 
 // Row r of the A operand (tensor memory), columns h0 .. h0 + HB - 1, from HB
-// float32 values: tf32 high parts at column 64 + h0, low parts at 128 + h0.
+// float32 values: tf32 high parts at column 128 + h0, low parts at 192 + h0.
 template <int HB>
 __device__ __forceinline__ void store_a_split_tmem(uint32_t tmem_row, int h0, const float (&v)[HB]) {
   float t[HB];
 #pragma unroll
-  for (int c = 0; c < HB; ++c) t[c] = to_tf32(v[c]);
+  for (int c = 0; c < HB; ++c) t[c] = tf32_trunc(v[c]);
   tmem_st<HB>(tmem_row + kColAhi + (uint32_t)h0, t);
 #pragma unroll
-  for (int c = 0; c < HB; ++c) t[c] = to_tf32(v[c] - to_tf32(v[c]));
+  for (int c = 0; c < HB; ++c) t[c] = v[c] - tf32_trunc(v[c]);
   tmem_st<HB>(tmem_row + kColAlo + (uint32_t)h0, t);
 }
 
-// The three tf32 products of one tile, accumulated in tensor memory (one thread).
+// S of the thread's row and columns h0 .. h0 + HB - 1: the sum of the two
+// accumulator halves.
+template <int HB, int Gp>
+__device__ __forceinline__ void load_s(uint32_t tmem_row, int h0, float (&s)[HB]) {
+  float s1[HB];
+  tmem_ld<HB>(tmem_row + (uint32_t)h0, s);
+  tmem_ld<HB>(tmem_row + (uint32_t)(Gp + h0), s1);
+  tmem_ld_wait();
+#pragma unroll
+  for (int c = 0; c < HB; ++c) s[c] += s1[c];
+}
+
+// The tf32 products of one tile (16 MMAs for Gp = 64), one thread.
 template <int Gp>
-__device__ __forceinline__ void issue_sigma_mma(uint32_t tmem, const float* Bhi, const float* Blo, uint64_t* bar) {
-  const uint32_t idesc = tf32_idesc(kTcRows, Gp);
-  const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
+__device__ __forceinline__ void issue_sigma_mma(uint32_t tmem, const float* Bhi, uint64_t* bar) {
+  const uint32_t id2 = tf32_idesc(kTcRows, 2 * Gp), id1 = tf32_idesc(kTcRows, Gp);
+  const uint32_t bh = smem_u32(Bhi);
 #pragma unroll
   for (int ks = 0; ks < Gp / 8; ++ks) {
-    const uint32_t ko = ks * 256;   // eight tf32 values of K: two core matrices of B
-    mma_tf32_ts(tmem, tmem + kColAhi + 8 * ks, kmajor_desc(bh + ko, Gp), idesc, ks > 0);
-    mma_tf32_ts(tmem, tmem + kColAhi + 8 * ks, kmajor_desc(bl + ko, Gp), idesc, 1);
-    mma_tf32_ts(tmem, tmem + kColAlo + 8 * ks, kmajor_desc(bh + ko, Gp), idesc, 1);
+    const uint64_t bd = kmajor_desc(bh + ks * 256, Gp);   // eight tf32 values of K: two core matrices
+    mma_tf32_ts(tmem, tmem + kColAhi + 8 * ks, bd, id2, ks > 0);   // A_hi [B_hi; B_lo]
+    mma_tf32_ts(tmem, tmem + kColAlo + 8 * ks, bd, id1, 1);        // + A_lo B_hi
   }
   mma_commit(bar);
 }
@@ -135,7 +159,6 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   const TcSmem L = tc_smem_layout(0, G, Gp, KK, np, TQ, NSQ, 0);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
   float* Bhi = reinterpret_cast<float*>(smraw + L.om);
-  float* Blo = Bhi + Gp * Gp;
   float* gs = reinterpret_cast<float*>(smraw + L.vec);
   float* us = gs + TV * G * KK;
   float* Ss = reinterpret_cast<float*>(smraw + L.tile);   // S of the tile being projected
@@ -157,11 +180,15 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   }
   __syncthreads();
   if (!anyp_s) return;   // every column already stopped: nothing changes
-  load_omega_split<Gp>(Om, G, Gq, Bhi, Blo);
+  load_omega_split<Gp>(Om, G, Gq, Bhi);
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
   const int ntiles = (int)((r1 - r0 + TV - 1) / TV);
   const int nsub = (int)((r1 - r0 + TQ - 1) / TQ);
   const int GK = G * KK;
+  // warps with column quads run the projection; the last warp, when it has
+  // none, issues the MMAs and the vector copies meanwhile
+  const int pwarps = (nq + 31) >> 5;
+  const int issuer = pwarps < kTcThreads / 32 ? kTcThreads - 32 : 0;
   if (tid == 0) {
     for (int q = 0; q < 2 + NSQ; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
@@ -177,8 +204,9 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   tc_fence_after();
   const uint32_t tmem = tslot;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);   // this warp's lane quarter
-  int vec_issued = 0, q_issued = 0, q_used = 0;   // (thread 0's bookkeeping)
+  int vec_issued = 0, q_issued = 0, q_used = 0;   // (bookkeeping of the issuing threads)
   bool mma_pending = false;
+  int mma_count = 0;
   auto issue_vec = [&](int tile) {
     const int64_t row0 = r0 + (int64_t)tile * TV;
     const int tr = (int)((r1 - row0) < TV ? (r1 - row0) : TV);
@@ -197,10 +225,9 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
     mbar_arrive_expect_tx(&bars[2 + slot], bytes);
     tma_load_1d(qring + (int64_t)slot * TQ * np, Q + row0 * np, bytes, &bars[2 + slot]);
   };
-  if (tid == 0) {
-    if (ntiles > 0) issue_vec(vec_issued++);
+  if (tid == issuer && ntiles > 0) issue_vec(vec_issued++);
+  if (tid == 0)
     for (; q_issued < NSQ && q_issued < nsub; ++q_issued) issue_q(q_issued);
-  }
   const int r = 32 * (warp & 3) + lane;   // MMA row of this thread: (t_r, j_r)
   const int t_r = r / KK, j_r = r % KK;
   const int hb = HB * (warp >> 2);
@@ -219,7 +246,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
     const int tr = it < ntiles ? (int)((r1 - row0) < TV ? (r1 - row0) : TV) : 0;
     float un[HB];
     if (it < ntiles) {
-      // E: u = g + mu u on the live columns; row r of the A operand
+      // E: u = g + mu u on the live columns, over the staged u; row r of the A operand
       lead_wait(&bars[0], it & 1, &abort_s, st.err);
       __syncthreads();
       if (abort_s) break;
@@ -232,24 +259,30 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
           const int e = (t_r * G + h) * KK + j_r;
           const float uo = us[e];
           v = act_j ? gs[e] + mu_j * uo : uo;
-          if (act_j) u[row0 * GK + e] = v;
+          if (act_j) us[e] = v;
           if (snap_j) wbest[row0 * GK + e] = w[row0 * GK + e];   // the w whose c is a new quarter-low
         }
         un[c] = v;
       }
       store_a_split_tmem<HB>(trow, hb, un);
       tmem_st_wait();
+      fence_proxy_async_smem();   // the staged u is written back by a bulk copy
       tc_fence_before();
       __syncthreads();
-      if (tid == 0) {
+      if (tid == issuer) {
         tc_fence_after();
-        if (vec_issued < ntiles) issue_vec(vec_issued++);   // the stage has been read: refill it
-        issue_sigma_mma<Gp>(tmem, Bhi, Blo, &bars[1]);
+        issue_sigma_mma<Gp>(tmem, Bhi, &bars[1]);
         mma_pending = true;
+        ++mma_count;
+        tma_store_1d(u + row0 * GK, us, (uint32_t)(tr * GK * sizeof(float)));
+        bulk_commit();
+        bulk_wait_read_all();   // the stage may be refilled once the store has read it
+        if (vec_issued < ntiles) issue_vec(vec_issued++);
       }
     }
-    if (it > 0) {
-      // P: projection partials of tile it - 1 (thread q owns column quad q)
+    if (it > 0 && warp < pwarps) {
+      // P: projection partials of tile it - 1 (thread q owns column quad q),
+      // by the warps that own column quads (named barrier 1)
       const int64_t prow0 = r0 + (int64_t)(it - 1) * TV;
       const int s0 = (it - 1) * (TV / TQ);
       const int s1 = min(nsub, s0 + TV / TQ);
@@ -257,7 +290,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
         const int slot = s % NSQ;
         lead_wait(&bars[2 + slot], (s / NSQ) & 1, &abort_s, st.err);
         if (tid == 0) q_used = s + 1;
-        __syncthreads();
+        named_bar_sync(1, 32 * pwarps);
         if (abort_s) break;
         const int64_t qrow0 = r0 + (int64_t)s * TQ;
         const int tq = (int)((r1 - qrow0) < TQ ? (r1 - qrow0) : TQ);
@@ -281,27 +314,26 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
             }
           }
         }
-        __syncthreads();
+        named_bar_sync(1, 32 * pwarps);
         if (tid == 0 && q_issued < nsub) issue_q(q_issued++);
       }
-      if (abort_s) break;
     }
+    __syncthreads();
+    if (abort_s) break;
     if (it < ntiles) {
       // R: S of tile it from tensor memory; d = u^T S; S into shared memory
       if (tid == 0) {
         if (!mbar_wait_bounded(&bars[1], it & 1, kWaitLimitNs)) {
           abort_s = 1;
           atomicExch(st.err, 1);
-        } else {
-          mma_pending = false;
         }
       }
       __syncthreads();
       if (abort_s) break;
+      if (tid == issuer) mma_pending = false;
       tc_fence_after();
       float sv[HB];
-      tmem_ld<HB>(trow + (uint32_t)hb, sv);
-      tmem_ld_wait();
+      load_s<HB, Gp>(trow, hb, sv);
       if (t_r < tr) {
         float dl = 0.f;
 #pragma unroll
@@ -319,11 +351,11 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
     }
   }
   if (abort_s) {
-    if (tid == 0) {
-      if (mma_pending) mbar_wait_bounded(&bars[1], (vec_issued - 1) & 1, kWaitLimitNs);
+    if (tid == issuer) {
+      if (mma_pending) mbar_wait_bounded(&bars[1], (mma_count - 1) & 1, kWaitLimitNs);
       drain_bar(bars, vec_issued, vec_issued - 1, 1);
-      drain_bar(bars + 2, q_issued, q_used, NSQ);
     }
+    if (tid == 0) drain_bar(bars + 2, q_issued, q_used, NSQ);
   } else {
     const double d = reduce_cols_strided<KK>(dsum, red);   // thread's column: tid % KK == j_r
     if (tid < KK) dpart[(int64_t)blockIdx.x * KK + tid] = d;
@@ -337,6 +369,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
               make_float4(acc[c][4 * a], acc[c][4 * a + 1], acc[c][4 * a + 2], acc[c][4 * a + 3]);
     }
   }
+  if (tid == issuer) bulk_wait_all();   // the stores of u have completed
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -365,7 +398,6 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
   uint64_t* gbar = bars + 2;
   uint64_t* qbar = bars + 2 + NSG;
   float* Bhi = reinterpret_cast<float*>(smraw + L.om);
-  float* Blo = Bhi + Gp * Gp;
   float* us = reinterpret_cast<float*>(smraw + L.vec);
   float* gstage = us + TV * G * KK;
   float* QCs = reinterpret_cast<float*>(smraw + L.tile);
@@ -386,7 +418,7 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
     }
   }
   if (tid < KK) lam_s[tid] = (float)st.lam[tid];
-  load_omega_split<Gp>(Om, G, Gq, Bhi, Blo);
+  load_omega_split<Gp>(Om, G, Gq, Bhi);
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
   const int ntiles = (int)((r1 - r0 + TV - 1) / TV);
   const int nsub = (int)((r1 - r0 + TQ - 1) / TQ);
@@ -434,6 +466,7 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
   tmem_st_wait();
   int u_issued = 0, g_issued = 0, g_used = 0, q_issued = 0, q_used = 0;
   bool mma_pending = false;
+  int mma_count = 0;
   auto tile_rows = [&](int tile) {
     const int64_t row0 = r0 + (int64_t)tile * TV;
     return (int)((r1 - row0) < TV ? (r1 - row0) : TV);
@@ -513,8 +546,9 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
     if (tid == 0) {
       tc_fence_after();
       if (u_issued < ntiles) issue_u(u_issued++);
-      issue_sigma_mma<Gp>(tmem, Bhi, Blo, &bars[1]);
+      issue_sigma_mma<Gp>(tmem, Bhi, &bars[1]);
       mma_pending = true;
+      ++mma_count;
     }
     if (tile + 1 < ntiles) load_w(tile + 1);
     // QC: (Q C)[t][i][j] = sum over block i's columns of Q[t][c] C[c][j] (pair threads)
@@ -581,8 +615,7 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
     {
       const float* gs = gstage + (int64_t)gslot * TV * GK;
       float sv[HB];
-      tmem_ld<HB>(trow + (uint32_t)hb, sv);
-      tmem_ld_wait();
+      load_s<HB, Gp>(trow, hb, sv);
       if (t_r < tr) {
         float cs = 0.f;
 #pragma unroll
@@ -607,7 +640,7 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
   }
   if (abort_s) {
     if (tid == 0) {
-      if (mma_pending) mbar_wait_bounded(&bars[1], (u_issued - 1) & 1, kWaitLimitNs);
+      if (mma_pending) mbar_wait_bounded(&bars[1], (mma_count - 1) & 1, kWaitLimitNs);
       drain_bar(bars, u_issued, u_issued - 1, 1);
       drain_bar(gbar, g_issued, g_used, NSG);
       drain_bar(qbar, q_issued, q_used, NSQ);

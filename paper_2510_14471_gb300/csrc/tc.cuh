@@ -167,4 +167,10 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// High tf32 part of x by truncation (the low 13 mantissa bits cleared): one
+// logic operation.  x - tf32_trunc(x) is exact in float32 and below 2^-10 |x|;
+// the tensor core reads only its leading 11 bits, so a split x = hi + lo
+// carries x to about 2^-21 relative.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 }  // namespace glmsur
