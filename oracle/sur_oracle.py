@@ -18,8 +18,11 @@ of General Linear Models"):
                              an eigen-split of Omega; zero-variance directions
                              become exact restrictions (Sec. 5.1 idea).
   * ``pcg``               -- Algorithm pcg on dense (G, K, h).
-  * ``sur_pcg_aug``       -- Algorithm glmpcg2 (PCG-Aug) with D = I in the SUR
-                             form of Sec. 5.3 (per-block QR, Sigma u = vec(U Omega)).
+  * ``sur_pcg_aug``       -- Algorithm glmpcg2 (PCG-Aug) in the SUR form of
+                             Sec. 5.3 (per-block QR, Sigma u = vec(U Omega)),
+                             D = I or D = diag(delta) (x) I_M (alpha I, diag(Sigma));
+                             also carries the z-iterates of Algorithm glmpcg.
+  * ``sur_pcg_aug3``      -- Algorithm glmpcg3 (s-recurrence), fixed steps.
   * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
                              Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
   * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
@@ -43,6 +46,7 @@ __all__ = [
     "sur_dense", "augmented_matrix", "aug_dense_solve", "gls_formula", "aug_lemma",
     "ols_blocks", "sur_gls_structured", "pcg", "sur_pcg_aug", "rglm_pcg_aug",
     "sur_gls_gradient", "sur_gls_gradient_kron", "sur_gls_refined", "augmented_residual", "lse_solve",
+    "sur_pcg_aug3", "jacobi_delta", "scaled_identity_delta",
 ]
 
 
@@ -267,13 +271,18 @@ def pcg(Gm, Km, h, x1, iters):
 
 
 class SurOps:
-    """The SUR applies of Sec. 5.3 with D = I, from thin QRs X_i = Q_i R_i:
-      Pi xi      = vec(xi_i - Q_i Q_i^T xi_i)
+    """The SUR applies of Sec. 5.3 from thin QRs X_i = Q_i R_i, with the
+    preconditioner block D = D_0 (x) I_M, D_0 = diag(delta) (D = I when delta
+    is not given).  From eq. (Xstar): X* = D^-1 X (X^T D^-1 X)^-1 and
+    Pi = (I - X* X^T) D^-1; with block i of D equal to delta_i I the delta_i
+    cancel in X* and
+      Pi xi      = vec((xi_i - Q_i Q_i^T xi_i) / delta_i)
+      P xi       = vec(xi_i - Q_i Q_i^T xi_i)      (orthogonal projector; Pi = P D^-1)
       X*^T xi    = vec(R_i^-1 Q_i^T xi_i)
       X v        = vec(X_i v_i)
       Sigma u    = vec(U Omega),  u = vec(U)."""
 
-    def __init__(self, X_blocks, Omega):
+    def __init__(self, X_blocks, Omega, delta=None):
         self.X = X_blocks
         self.Omega = np.asarray(Omega, dtype=float)
         self.G = len(X_blocks)
@@ -281,6 +290,7 @@ class SurOps:
         self.n_i = [x.shape[1] for x in X_blocks]
         self.offs = np.cumsum([0] + self.n_i)
         self.QR = [np.linalg.qr(Xi) for Xi in X_blocks]
+        self.delta = np.ones(self.G) if delta is None else np.asarray(delta, dtype=float)
 
     def sigma(self, u):
         # (U Omega)_h = sum_g U_g omega_gh: with the G columns of every U_j as
@@ -289,13 +299,20 @@ class SurOps:
         U = u.reshape(self.G, self.M * k)
         return (self.Omega.T @ U).reshape(self.G * self.M, k)
 
-    def pi(self, xi):
+    def proj(self, xi):
         out = np.empty_like(xi)
         M = self.M
         for i, (Qi, _) in enumerate(self.QR):
             blk = xi[i * M:(i + 1) * M]
             out[i * M:(i + 1) * M] = blk - Qi @ (Qi.T @ blk)
         return out
+
+    def dinv(self, xi):
+        """D^-1 xi (block i divided by delta_i)."""
+        return xi / np.repeat(self.delta, self.M)[:, None]
+
+    def pi(self, xi):
+        return self.dinv(self.proj(xi))
 
     def xstar_t(self, xi):
         M = self.M
@@ -323,15 +340,20 @@ STATUS_NOT_CONVERGED = "not_converged"
 
 
 def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
-                record=False, ops=None, w1=None):
-    """Algorithm glmpcg2 (PCG-Aug) with D = I in the SUR form of Sec. 5.3 (O3).
+                record=False, ops=None, w1=None, delta=None):
+    """Algorithm glmpcg2 (PCG-Aug) in the SUR form of Sec. 5.3 (O3), with the
+    preconditioner block D = diag(delta) (x) I_M (D = I by default; Sec. 3.3
+    and the VAR experiments use D = alpha I and D = diag(Sigma)).
 
     One independent PCG per column of Y (each with its own c, d, lambda, mu).
     Start: w_1 = 0 (or ``w1`` with X^T w_1 = 0), z_1 = 0.
-    With D = I, Pi is symmetric and idempotent, so c = r^T Pi r is evaluated
-    as (Pi r)^T (Pi r): the same quantity, without the cancellation of the
-    large range-space part of r against Pi r (which floors sqrt(c/c_1) near
-    sqrt(eps) when written as r . (Pi r)).
+    Pi = P D^-1 with P the orthogonal projector onto null(X^T) and D commuting
+    with P block by block, so c = r^T Pi r is evaluated as (P r)^T D^-1 (P r):
+    the same quantity, without the cancellation of the large range-space
+    part of r against Pi r (which floors sqrt(c/c_1) near sqrt(eps) when
+    written as r . (Pi r)).
+    The z-iterates of Algorithm glmpcg (z_{i+1} = z_i - lambda_i v_i) are
+    carried too and returned as ``z``.
     Stop a column when sqrt(c_{i+1}/c_1) <= tol (converged), when d_i <= 0 or
     is not finite (breakdown), when c has not reached a new minimum for W
     steps (stagnation: c no longer decreases, Sec. 3.2; c_i need
@@ -339,7 +361,7 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     used), or at ``maxit``.  Every column returns its last iterate w and
     z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
     Returns dict(b, w, iters, status, relres[, history])."""
-    op = ops if ops is not None else SurOps(X_blocks, Omega)
+    op = ops if ops is not None else SurOps(X_blocks, Omega, delta)
     m = op.G * op.M
     Y = np.asarray(Y, dtype=float).reshape(m, -1)
     k = Y.shape[1]
@@ -349,9 +371,10 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     w = np.zeros((m, k)) if w1 is None else np.array(w1, dtype=float).reshape(m, k)
     z = np.zeros((n, k))
     r = op.sigma(w) + op.xmul(z) - Y                          # step 2
-    Pr = op.pi(r)
-    c = np.sum(Pr * Pr, axis=0)                               # r^T Pi r, Pi = Pi^T Pi
-    u = Pr.copy()                                             # step 3
+    Pr = op.proj(r)
+    Pir = op.dinv(Pr)                                         # Pi r
+    c = np.sum(Pr * Pir, axis=0)                              # r^T Pi r
+    u = Pir.copy()                                            # step 3
     v = op.xstar_t(r)
     c1 = c.copy()
     active = c1 > 0
@@ -373,9 +396,11 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
         active &= ~bad
         lam = np.where(active, c / np.where(active, dd, 1.0), 0.0)
         w = w - lam * u                                       # step 6
+        z = z - lam * v                                       # (Algorithm glmpcg)
         r = r - lam * (Su + op.xmul(v))                       # step 7
-        Pr = op.pi(r)
-        c_new = np.where(active, np.sum(Pr * Pr, axis=0), c)  # step 8
+        Pr = op.proj(r)
+        Pir = op.dinv(Pr)
+        c_new = np.where(active, np.sum(Pr * Pir, axis=0), c)  # step 8
         iters = iters + active
         rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
         relres = np.where(active, rr, relres)
@@ -396,16 +421,64 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
         active &= ~stag
         mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
         v = op.xstar_t(r) + mu * v                            # step 12
-        u = np.where(active, Pr + mu * u, u)
+        u = np.where(active, Pir + mu * u, u)
         c = np.where(active, c_new, c)
         if record:
             hist["w"].append(w.copy()); hist["r"].append(r.copy())
             hist["u"].append(u.copy()); hist["c"].append(c_new.copy())
     b = op.xstar_t(Y - op.sigma(w))                           # step 10
-    out = dict(b=b, w=w, iters=iters, status=list(status), relres=relres)
+    out = dict(b=b, w=w, z=z, iters=iters, status=list(status), relres=relres)
     if record:
         out["history"] = hist
     return out
+
+
+def sur_pcg_aug3(X_blocks, Omega, Y, iters, delta=None, ops=None):
+    """Algorithm glmpcg3 (the alternative PCG-Aug) in the SUR form, for a
+    fixed number of steps and without stop tests (its iterates are compared
+    with those of Algorithm glmpcg2, which it equals in exact arithmetic).
+    It carries s_i (s_1 = r_1, s_{i+1} = r_{i+1} + mu_i s_i) in place of u_i
+    and v_i: d_i = s_i^T Pi Sigma Pi s_i, w_{i+1} = w_i - lambda_i Pi s_i,
+    r_{i+1} = r_i - lambda_i (Sigma Pi + X X*^T) s_i.  Start w_1 = 0, z_1 = 0.
+    Returns dict(b, w, history: list of w iterates and of c)."""
+    op = ops if ops is not None else SurOps(X_blocks, Omega, delta)
+    m = op.G * op.M
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    k = Y.shape[1]
+    w = np.zeros((m, k))
+    r = op.sigma(w) - Y                                       # step 2 (z_1 = 0)
+    Pr = op.proj(r)
+    c = np.sum(Pr * op.dinv(Pr), axis=0)
+    s = r.copy()                                              # step 3
+    ws, cs = [w.copy()], [c.copy()]
+    for _ in range(iters):
+        Pis = op.pi(s)
+        SPis = op.sigma(Pis)
+        dd = np.sum(Pis * SPis, axis=0)                       # step 5
+        lam = c / dd
+        w = w - lam * Pis                                     # step 6
+        r = r - lam * (SPis + op.xmul(op.xstar_t(s)))         # step 7
+        Pr = op.proj(r)
+        c_new = np.sum(Pr * op.dinv(Pr), axis=0)              # step 8
+        mu = c_new / c
+        s = r + mu * s                                        # step 12
+        c = c_new
+        ws.append(w.copy()); cs.append(c.copy())
+    b = op.xstar_t(Y - op.sigma(w))
+    return dict(b=b, w=w, history={"w": ws, "c": cs})
+
+
+def jacobi_delta(Omega):
+    """D_0 = diag(Sigma_0): the diagonal preconditioner block of the VAR
+    experiments (D = diag(Sigma) = diag(Omega) (x) I_M for the SUR model)."""
+    return np.diag(np.asarray(Omega, dtype=float)).copy()
+
+
+def scaled_identity_delta(Omega):
+    """D_0 = alpha I with alpha = max_i Sigma_ii (the other choice of the VAR
+    experiments)."""
+    Om = np.asarray(Omega, dtype=float)
+    return np.full(Om.shape[0], np.max(np.diag(Om)))
 
 
 def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=25):
