@@ -77,7 +77,24 @@ typedef struct {
                              n <= 2048 and W = [X_1 ... X_G] has full column
                              rank (otherwise the model is kept whole)         */
   int step_kernels;       /* GLM_SUR_STEP_*: kernels of the float32 bulk steps   */
+  int precond;            /* GLM_SUR_PRECOND_*: the block D of the preconditioner
+                             of eq. (invprec), D = D0 (x) I_M               */
 } glm_sur_opts;
+
+enum {
+  GLM_SUR_PRECOND_IDENTITY = 0,  /* D = I (Sec. 5.3)                             */
+  GLM_SUR_PRECOND_SCALED = 1,    /* D = alpha I, alpha = max_i omega_ii          */
+  GLM_SUR_PRECOND_DIAG = 2       /* D = diag(Sigma) = diag(Omega) (x) I_M (the two
+                                    choices of the VAR experiments).  With D0 =
+                                    diag(delta), PCG-Aug with D runs the iterates
+                                    of PCG-Aug with D = I on the row-scaled model
+                                    (y_i, X_i divided by sqrt(delta_i), Omega by
+                                    sqrt(delta_a delta_b)); solves run that model
+                                    and return the same b.  relres refers to it;
+                                    a delta_i <= 0 is taken as 1.  Not with
+                                    restrictions, glm_sur_backward or
+                                    glm_sur_get_w (GLM_SUR_INVALID_ARG).        */
+};
 
 enum {
   GLM_SUR_STEP_AUTO = 0,  /* fused two-pass step with the Sigma-apply on the
@@ -89,7 +106,8 @@ enum {
 };
 
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
- * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0, step_kernels AUTO.  A column that stops without
+ * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0, step_kernels AUTO,
+ * precond IDENTITY.  A column that stops without
  * converging (stagnation, breakdown, maxit) returns its best saved iterate:
  * w is saved whenever c falls below a quarter of the c of the previous save. */
 void glm_sur_default_opts(glm_sur_opts* opts);

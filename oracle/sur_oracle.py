@@ -23,6 +23,8 @@ of General Linear Models"):
                              D = I or D = diag(delta) (x) I_M (alpha I, diag(Sigma));
                              also carries the z-iterates of Algorithm glmpcg.
   * ``sur_pcg_aug3``      -- Algorithm glmpcg3 (s-recurrence), fixed steps.
+  * ``pcg_ne``            -- the PCG-NE comparator: CG on the normal equations
+                             with Sigma^-1 = Omega^-1 (x) I_M (PD Omega).
   * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
                              Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
   * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
@@ -46,7 +48,7 @@ __all__ = [
     "sur_dense", "augmented_matrix", "aug_dense_solve", "gls_formula", "aug_lemma",
     "ols_blocks", "sur_gls_structured", "pcg", "sur_pcg_aug", "rglm_pcg_aug",
     "sur_gls_gradient", "sur_gls_gradient_kron", "sur_gls_refined", "augmented_residual", "lse_solve",
-    "sur_pcg_aug3", "jacobi_delta", "scaled_identity_delta",
+    "sur_pcg_aug3", "jacobi_delta", "scaled_identity_delta", "pcg_ne",
 ]
 
 
@@ -466,6 +468,69 @@ def sur_pcg_aug3(X_blocks, Omega, Y, iters, delta=None, ops=None):
         ws.append(w.copy()); cs.append(c.copy())
     b = op.xstar_t(Y - op.sigma(w))
     return dict(b=b, w=w, history={"w": ws, "c": cs})
+
+
+def pcg_ne(X_blocks, Omega, Y, tol=1e-13, maxit=None, record=False):
+    """PCG-NE, the comparator of the Monte-Carlo study and of the SUR and VAR
+    experiments: the conjugate gradient method (Algorithm pcg with K = I, no
+    preconditioner) on the normal equations (X^T Sigma^-1 X) beta =
+    X^T Sigma^-1 y, with Sigma^-1 = Omega^-1 (x) I_M applied as U Omega^-1 and
+    X, X^T block by block.  One CG per column of Y, x_1 = 0; a column stops
+    when ||h - A beta|| <= tol ||h|| (h = X^T Sigma^-1 y) or at maxit
+    (default n, the number of distinct eigenvalues at most).  Omega must be
+    positive definite.  Returns dict(b, iters, status, relres[, history])."""
+    op = SurOps(X_blocks, Omega)
+    Oinv = np.linalg.inv(op.Omega)
+    G, M = op.G, op.M
+    n = int(op.offs[-1])
+    Y = np.asarray(Y, dtype=float).reshape(G * M, -1)
+    k = Y.shape[1]
+    if maxit is None:
+        maxit = n
+
+    def sigma_inv(u):
+        U = u.reshape(G, M * u.shape[1])
+        return (Oinv.T @ U).reshape(G * M, u.shape[1])
+
+    def apply_a(v):
+        return op.xt(sigma_inv(op.xmul(v)))
+
+    h = op.xt(sigma_inv(Y))
+    beta = np.zeros((n, k))
+    f = apply_a(beta) - h                          # f = G x - h of Algorithm pcg
+    p = f.copy()
+    c = np.sum(f * f, axis=0)
+    c1 = c.copy()
+    active = c1 > 0
+    iters = np.zeros(k, dtype=int)
+    status = np.array([STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active], dtype=object)
+    relres = np.where(c1 > 0, 1.0, 0.0)
+    hist = [beta.copy()] if record else None
+    for _ in range(maxit):
+        if not active.any():
+            break
+        Ap = apply_a(p)
+        dd = np.sum(p * Ap, axis=0)
+        lam = np.where(active, c / np.where(active & (dd != 0), dd, 1.0), 0.0)
+        beta = beta - lam * p
+        f = f - lam * Ap
+        c_new = np.sum(f * f, axis=0)
+        iters = iters + active
+        rr = np.sqrt(c_new / np.where(c1 > 0, c1, 1.0))
+        relres = np.where(active, rr, relres)
+        conv = active & (rr <= tol)
+        for j in np.where(conv)[0]:
+            status[j] = STATUS_CONVERGED
+        active &= ~conv
+        mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
+        p = np.where(active, f + mu * p, p)
+        c = np.where(active, c_new, c)
+        if record:
+            hist.append(beta.copy())
+    out = dict(b=beta, iters=iters, status=list(status), relres=relres)
+    if record:
+        out["history"] = hist
+    return out
 
 
 def jacobi_delta(Omega):

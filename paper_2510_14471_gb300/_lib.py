@@ -33,12 +33,16 @@ GLM_SUR_PREC_FP32_REFINE = 1
 GLM_SUR_STEP_AUTO = 0
 GLM_SUR_STEP_SIMT = 1
 
+GLM_SUR_PRECOND_IDENTITY = 0
+GLM_SUR_PRECOND_SCALED = 1
+GLM_SUR_PRECOND_DIAG = 2
+
 
 class GlmSurOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("stagnation_window", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("chunk", ctypes.c_int), ("inner_shift", ctypes.c_double),
-                ("reduce_rows", ctypes.c_int), ("step_kernels", ctypes.c_int)]
+                ("reduce_rows", ctypes.c_int), ("step_kernels", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 # (name, restype, argtypes) of every exported entry point

@@ -66,8 +66,11 @@ struct glm_sur_ctx {
   double* Q64 = nullptr;
   float* Q32 = nullptr;
   double* R = nullptr;
-  double* Om64 = nullptr;
+  double* Om64 = nullptr;      // Omega of the iteration (scaled: D0^-1/2 Omega D0^-1/2 when precond != identity)
   float* Om32 = nullptr;
+  double* Omraw = nullptr;     // Omega as given
+  double* d_sqrtd = nullptr;   // sqrt(delta_i) and 1 / sqrt(delta_i) of the preconditioner block (G each)
+  double* d_isqrtd = nullptr;
   int* setup_flags = nullptr;
   // solve workspace (capacity kcap right-hand sides)
   int kcap = 0;
@@ -139,6 +142,7 @@ glm_sur_status validate_opts(const glm_sur_opts* o) {
   if (o->chunk < 2 || (o->chunk & 1)) return GLM_SUR_INVALID_ARG;
   if (!(o->inner_shift >= 0.0) || o->inner_shift > 1e-2) return GLM_SUR_INVALID_ARG;
   if (o->step_kernels != GLM_SUR_STEP_AUTO && o->step_kernels != GLM_SUR_STEP_SIMT) return GLM_SUR_INVALID_ARG;
+  if (o->precond < GLM_SUR_PRECOND_IDENTITY || o->precond > GLM_SUR_PRECOND_DIAG) return GLM_SUR_INVALID_ARG;
   return GLM_SUR_OK;
 }
 
@@ -579,7 +583,8 @@ glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, 
     h->launches += 4;
     return GLM_SUR_OK;
   }
-  launch_tri_solve(h->gm, k, h->R, h->C64, b, ldb, s);
+  // (a row-scaled model has R_i / sqrt(delta_i): b_i = sqrt(delta_i) R_i^-1 Q_i^T (y' - Sigma' w')_i)
+  launch_tri_solve(h->gm, k, h->R, h->C64, b, ldb, s, h->opts.precond ? h->d_sqrtd : nullptr);
   h->launches += 4;
   GS_CUDA_TRY(cudaGetLastError());
   return GLM_SUR_OK;
@@ -683,6 +688,28 @@ glm_sur_status rotate_in(glm_sur_ctx* h, const double* Y, int64_t ldy, int k, cu
   return GLM_SUR_OK;
 }
 
+// Omega of the iteration from the given one: for the preconditioner block
+// D = D0 (x) I_M (D0 = alpha I or diag(Omega), eq. invprec with the choices of
+// the VAR experiments), PCG-Aug on (y, X, Sigma) with D runs the iterates of
+// PCG-Aug with D = I on the row-scaled model (S y, S X, S Sigma S), S =
+// D0^-1/2 (x) I_M: the augmented matrices are congruent by diag(S, I), so KG
+// is similar and w' = S^-1 w, while the GLS estimator is unchanged.  Here
+// Omega' = D0^-1/2 Omega D0^-1/2; the solve scales y and b.
+glm_sur_status derive_omega(glm_sur_ctx* h, cudaStream_t s) {
+  const Geom& gm = h->gm;
+  if (h->opts.precond == GLM_SUR_PRECOND_IDENTITY) {
+    GS_CUDA_TRY(cudaMemcpyAsync(h->Om64, h->Omraw, sizeof(double) * (size_t)gm.G * gm.Gq, cudaMemcpyDeviceToDevice,
+                                s));
+  } else {
+    launch_precond_omega(gm.G, gm.Gq, h->opts.precond, h->Omraw, h->Om64, h->d_sqrtd, h->d_isqrtd, s);
+  }
+  launch_convert<double, float>((int64_t)gm.G * gm.Gq, h->Om64, h->Om32, 1.0, s);
+  // float32 copy used only by the inner solves of FP32_REFINE: Omega + s I
+  launch_shift_diag(gm.G, gm.Gq, h->Om64, h->Om32, h->opts.inner_shift, s);
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -702,6 +729,7 @@ void glm_sur_default_opts(glm_sur_opts* o) {
   o->inner_shift = 0.0;
   o->reduce_rows = 0;
   o->step_kernels = GLM_SUR_STEP_AUTO;
+  o->precond = GLM_SUR_PRECOND_IDENTITY;
 }
 
 const char* glm_sur_status_string(glm_sur_status s) {
@@ -830,6 +858,9 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   SETUP_TRY(dalloc(&h->R, (size_t)r_off[G]));
   SETUP_TRY(dalloc(&h->Om64, (size_t)G * gm.Gq));
   SETUP_TRY(dalloc(&h->Om32, (size_t)G * gm.Gq));
+  SETUP_TRY(dalloc(&h->Omraw, (size_t)G * gm.Gq));
+  SETUP_TRY(dalloc(&h->d_sqrtd, (size_t)G));
+  SETUP_TRY(dalloc(&h->d_isqrtd, (size_t)G));
   SETUP_TRY(dalloc(&h->setup_flags, 1));
   SETUP_TRY(cudaMemsetAsync(h->Q64, 0, sizeof(double) * (size_t)M * gm.np, s));
   SETUP_TRY(cudaMemsetAsync(h->setup_flags, 0, sizeof(int), s));
@@ -871,13 +902,11 @@ glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_strea
   if (!h || !Omega) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const Geom& gm = h->gm;
-  GS_CUDA_TRY(cudaMemsetAsync(h->Om64, 0, sizeof(double) * (size_t)gm.G * gm.Gq, s));
-  GS_CUDA_TRY(cudaMemcpy2DAsync(h->Om64, gm.Gq * sizeof(double), Omega, gm.G * sizeof(double),
+  GS_CUDA_TRY(cudaMemsetAsync(h->Omraw, 0, sizeof(double) * (size_t)gm.G * gm.Gq, s));
+  GS_CUDA_TRY(cudaMemcpy2DAsync(h->Omraw, gm.Gq * sizeof(double), Omega, gm.G * sizeof(double),
                                 gm.G * sizeof(double), gm.G, cudaMemcpyDeviceToDevice, s));
-  launch_convert<double, float>((int64_t)gm.G * gm.Gq, h->Om64, h->Om32, 1.0, s);
-  // float32 copy used only by the inner solves of FP32_REFINE: Omega + s I
-  launch_shift_diag(gm.G, gm.Gq, h->Om64, h->Om32, h->opts.inner_shift, s);
-  GS_CUDA_TRY(cudaGetLastError());
+  glm_sur_status rc = derive_omega(h, s);
+  if (rc != GLM_SUR_OK) return rc;
   h->has_w = false;
   return GLM_SUR_OK;
 }
@@ -901,8 +930,8 @@ glm_sur_status glm_sur_set_opts(glm_sur_t h, const glm_sur_opts* opts) {
     GS_CUDA_TRY(cudaDeviceSynchronize());
   }
   if (prec_change) free_workspace(h);
-  launch_convert<double, float>((int64_t)h->gm.G * h->gm.Gq, h->Om64, h->Om32, 1.0, nullptr);
-  launch_shift_diag(h->gm.G, h->gm.Gq, h->Om64, h->Om32, h->opts.inner_shift, nullptr);
+  glm_sur_status rc = derive_omega(h, nullptr);
+  if (rc != GLM_SUR_OK) return rc;
   GS_CUDA_TRY(cudaDeviceSynchronize());
   h->plan_k = -1;
   return GLM_SUR_OK;
@@ -1067,11 +1096,14 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
   const int64_t m = gm.M * gm.G;
   if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
   if (h->kc > 0 && (h->opts.precision != GLM_SUR_PREC_FP64 || (d && ldd < h->kc))) return GLM_SUR_INVALID_ARG;
+  if (h->kc > 0 && h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;
   IterPlan p64;
   glm_sur_status rc = prepare_solve(h, k, p64);
   if (rc != GLM_SUR_OK) return rc;
   h->has_w = false;
-  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
+  // preconditioner block D = D0 (x) I_M: the iteration runs on the row-scaled
+  // model (y_i / sqrt(delta_i), X_i / sqrt(delta_i), D0^-1/2 Omega D0^-1/2)
+  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s, h->opts.precond ? h->d_isqrtd : nullptr);
   h->launches += 1;
   GS_CUDA_TRY(cudaGetLastError());
   rc = solve_core(h, p64, d, ldd, k, b, ldb, iters, relres, s);
@@ -1120,6 +1152,7 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
 glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY, int64_t ldy,
                                 double* dL_dOmega, int64_t ldo, int* iters, double* relres, glm_sur_stream_t stream) {
   if (!h || !dL_db || (!dL_dY && !dL_dOmega)) return GLM_SUR_INVALID_ARG;
+  if (h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;
   if (h->sub) {
     // the adjoint of the reduced model; dL/dy = Q dL/dy' (the rows outside
     // range(W) have lam = 0) and dL/dOmega is the reduced model's
@@ -1223,6 +1256,7 @@ glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
 glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream) {
   if (h && h->sub) return GLM_SUR_INVALID_ARG;   // w of the unreduced rows is not formed
   if (!h || !w || !h->has_w || ldw < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
+  if (h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;   // w of the row-scaled model
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_layout_to_colmajor<double>(h->gm, h->last_k, h->w64, w, ldw, s);
   GS_CUDA_TRY(cudaGetLastError());
@@ -1362,6 +1396,7 @@ void glm_sur_destroy(glm_sur_t h) {
   cudaDeviceSynchronize();
   free_workspace(h);
   dfree(h->Q64); dfree(h->Q32); dfree(h->R); dfree(h->Om64); dfree(h->Om32); dfree(h->setup_flags);
+  dfree(h->Omraw); dfree(h->d_sqrtd); dfree(h->d_isqrtd);
   dfree(h->gm.d_n_i); dfree(h->gm.d_off); dfree(h->gm.d_poff); dfree(h->gm.d_quad_blk); dfree(h->gm.d_r_off);
   dfree(h->gm.d_ug_blk0); dfree(h->gm.d_col_blk);
   dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);

@@ -1138,10 +1138,11 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
 // layout conversions and small helpers
 // ---------------------------------------------------------------------------
 
-// out[(t*G + i)*k + j] = scale * Y[j*ldy + i*M + t]   (32 x 32 tiles over (t, c = i*k + j))
+// out[(t*G + i)*k + j] = scale * s_i * Y[j*ldy + i*M + t]   (32 x 32 tiles over
+// (t, c = i*k + j)); s_i = blk_scale[i], or 1 when blk_scale is null
 template <typename Tout>
 __global__ void k_colmajor_to_layout(int64_t M, int G, int k, const double* __restrict__ Y, int64_t ldy,
-                                     Tout* __restrict__ out, double scale) {
+                                     Tout* __restrict__ out, double scale, const double* __restrict__ blk_scale) {
   __shared__ double tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32;
   const int64_t c0 = (int64_t)blockIdx.y * 32;
@@ -1159,7 +1160,10 @@ __global__ void k_colmajor_to_layout(int64_t M, int G, int k, const double* __re
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int64_t t = t0 + r, c = c0 + tx;
-    if (t < M && c < ncol) out[t * ncol + c] = (Tout)(scale * tile[tx][r]);
+    if (t < M && c < ncol) {
+      const double sc = blk_scale ? scale * blk_scale[c / k] : scale;
+      out[t * ncol + c] = (Tout)(sc * tile[tx][r]);
+    }
   }
 }
 
@@ -1186,10 +1190,12 @@ __global__ void k_layout_to_colmajor(int64_t M, int G, int k, const Tin* __restr
   }
 }
 
-// b_i = R_i^-1 C_i  (back substitution; one thread per (block, column))
+// b_i = s_i R_i^-1 C_i  (back substitution; one thread per (block, column));
+// s_i = blk_scale[i], or 1 when blk_scale is null
 __global__ void k_tri_solve(int G, int k, const double* __restrict__ R, const int64_t* __restrict__ r_off,
                             const int* __restrict__ n_i, const int* __restrict__ off,
-                            const int* __restrict__ poff, const double* __restrict__ C, double* b, int64_t ldb) {
+                            const int* __restrict__ poff, const double* __restrict__ C, double* b, int64_t ldb,
+                            const double* __restrict__ blk_scale) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= G * k) return;
   const int i = id / k, j = id % k;
@@ -1201,7 +1207,34 @@ __global__ void k_tri_solve(int G, int k, const double* __restrict__ R, const in
     for (int c = r + 1; c < ni; ++c) s -= Ri[r * ni + c] * x[c];
     x[r] = s / Ri[r * ni + r];
   }
-  for (int r = 0; r < ni; ++r) b[(int64_t)j * ldb + off[i] + r] = x[r];
+  const double sc = blk_scale ? blk_scale[i] : 1.0;
+  for (int r = 0; r < ni; ++r) b[(int64_t)j * ldb + off[i] + r] = sc * x[r];
+}
+
+// Preconditioner block D = diag(delta) (x) I_M by row scaling: delta_i =
+// omega_ii (kind 2) or max_i omega_ii (kind 1); Om_out = D0^-1/2 Om D0^-1/2,
+// sqrtd[i] = sqrt(delta_i), isqrtd[i] = 1 / sqrt(delta_i).  A block whose
+// delta is not positive keeps delta_i = 1.  One CTA.
+__global__ void k_precond_omega(int G, int Gq, int kind, const double* __restrict__ Om, double* __restrict__ Om_out,
+                                double* __restrict__ sqrtd, double* __restrict__ isqrtd) {
+  __shared__ double dmax;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < G; ++i) mx = fmax(mx, Om[(int64_t)i * Gq + i]);
+    dmax = mx;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    double d = kind == 1 ? dmax : Om[(int64_t)i * Gq + i];
+    if (!(d > 0.0) || !isfinite(d)) d = 1.0;
+    sqrtd[i] = sqrt(d);
+    isqrtd[i] = 1.0 / sqrt(d);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < G * Gq; e += blockDim.x) {
+    const int a = e / Gq, c = e % Gq;
+    Om_out[e] = c < G ? Om[e] * isqrtd[a] * isqrtd[c] : 0.0;
+  }
 }
 
 template <typename Tin, typename Tout>
@@ -1448,9 +1481,9 @@ void launch_proj_update(const IterPlan& p, const Geom& gm, int k, const T* Q, co
 
 template <typename Tout>
 void launch_colmajor_to_layout(const Geom& gm, int k, const double* Y, int64_t ldy, Tout* out, double scale,
-                               cudaStream_t s) {
+                               cudaStream_t s, const double* blk_scale) {
   dim3 grid((unsigned)ceil_div(gm.M, 32), (unsigned)ceil_div((int64_t)gm.G * k, 32));
-  k_colmajor_to_layout<Tout><<<grid, 256, 0, s>>>(gm.M, gm.G, k, Y, ldy, out, scale);
+  k_colmajor_to_layout<Tout><<<grid, 256, 0, s>>>(gm.M, gm.G, k, Y, ldy, out, scale, blk_scale);
 }
 template <typename Tin>
 void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s) {
@@ -1459,10 +1492,14 @@ void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, 
 }
 
 void launch_tri_solve(const Geom& gm, int k, const double* R, const double* C, double* b, int64_t ldb,
-                      cudaStream_t s) {
+                      cudaStream_t s, const double* blk_scale) {
   const int n = gm.G * k;
   k_tri_solve<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(gm.G, k, R, gm.d_r_off, gm.d_n_i, gm.d_off, gm.d_poff, C,
-                                                        b, ldb);
+                                                        b, ldb, blk_scale);
+}
+void launch_precond_omega(int G, int Gq, int kind, const double* Om, double* Om_out, double* sqrtd, double* isqrtd,
+                          cudaStream_t s) {
+  k_precond_omega<<<1, 256, 0, s>>>(G, Gq, kind, Om, Om_out, sqrtd, isqrtd);
 }
 template <typename Tin, typename Tout>
 void launch_convert(int64_t n, const Tin* in, Tout* out, double scale, cudaStream_t s) {
@@ -1548,7 +1585,7 @@ template void launch_proj_update<float>(const IterPlan&, const Geom&, int, const
                                         const float*, int, const double*, double, double*, const PcgState&, int,
                                         cudaStream_t);
 template void launch_colmajor_to_layout<double>(const Geom&, int, const double*, int64_t, double*, double,
-                                                cudaStream_t);
+                                                cudaStream_t, const double*);
 template void launch_layout_to_colmajor<double>(const Geom&, int, const double*, double*, int64_t, cudaStream_t);
 template void launch_convert<double, float>(int64_t, const double*, float*, double, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);

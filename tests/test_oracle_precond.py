@@ -98,3 +98,67 @@ def test_jacobi_block_helps_a_badly_scaled_omega():
     assert jac["status"] == [O.STATUS_CONVERGED] and jac["iters"][0] <= 30, jac["iters"]
     assert rel(jac["b"], b_dense) < 1e-11
     assert rel(plain["b"], b_dense) > 1e3 * rel(jac["b"], b_dense)
+
+
+# ---------------------------------------------------------------- PCG-NE comparator
+
+def test_pcg_ne_matches_generic_cg_on_the_normal_matrix():
+    # Algorithm pcg with K = I on the dense normal matrix A = X^T Sigma^-1 X
+    # fixes the iterates of the matrix-free SUR version
+    p = S.make_problem(G=3, M=20, n_i=[2, 3, 2], k=1, seed=51, omega="chol")
+    Sigma, X = O.sur_dense(p.X_blocks, p.Omega)
+    Sinv = np.linalg.inv(Sigma)
+    A = X.T @ Sinv @ X
+    h = X.T @ Sinv @ p.Y[:, 0]
+    xs = O.pcg(A, np.eye(A.shape[0]), h, np.zeros(A.shape[0]), 5)
+    res = O.pcg_ne(p.X_blocks, p.Omega, p.Y, tol=0.0, maxit=5, record=True)
+    for i in range(1, len(xs)):
+        assert rel(res["history"][i][:, 0], xs[i]) < 1e-9, i
+
+
+def test_pcg_ne_converges_to_gls_within_n_steps():
+    # exact arithmetic: at most n steps (n distinct eigenvalues at most);
+    # the limit is eq. (GLS)
+    p = S.make_problem(G=4, M=50, n_i=[3, 2, 4, 3], k=2, seed=53, omega="spectrum")
+    res = O.pcg_ne(p.X_blocks, p.Omega, p.Y, tol=1e-13, maxit=4 * p.n)
+    assert all(s == O.STATUS_CONVERGED for s in res["status"])
+    assert max(res["iters"]) <= p.n + 2
+    assert rel(res["b"], O.gls_formula(p.X_blocks, p.Omega, p.Y)) < 1e-10
+
+
+def test_pcg_ne_steps_equal_the_distinct_eigenvalues():
+    # orthonormal X_i and diagonal Omega: X^T Sigma^-1 X = blockdiag(I / omega_ii),
+    # whose distinct eigenvalues are the distinct omega_ii; CG ends after
+    # exactly that many steps
+    g = S.rng(59)
+    G, M = 5, 40
+    X = [np.linalg.qr(x)[0] for x in S.gaussian_blocks(g, M, [3, 2, 3, 2, 3])]
+    Om = np.diag([1.0, 2.0, 5.0, 5.0, 0.5])
+    Y, _ = S.draw_responses(g, X, np.linalg.cholesky(Om), M, 2)
+    res = O.pcg_ne(X, Om, Y, tol=1e-12)
+    assert list(res["iters"]) == [4, 4]
+    assert rel(res["b"], O.gls_formula(X, Om, Y)) < 1e-12
+
+
+def test_pcg_ne_loses_finite_termination_on_ill_conditioned_x():
+    # regressors with singular values over five orders: cond(X^T Sigma^-1 X)
+    # ~ 1e10 and PCG-NE needs several times n steps, while PCG-Aug (whose
+    # projection does not see cond(X)) needs fewer than n + 10 (the VAR
+    # experiments: PCG-NE stalls on ill-conditioned normal systems)
+    g = S.rng(57)
+    G, M = 5, 40
+    X = S.gaussian_blocks(g, M, [3, 2, 3, 2, 3])
+    for i in range(G):
+        U, s, Vt = np.linalg.svd(X[i], full_matrices=False)
+        X[i] = U @ np.diag(np.logspace(0, -5, len(s))) @ Vt
+    A = g.standard_normal((G, G))
+    Om = A @ A.T / G + np.eye(G)
+    Y, _ = S.draw_responses(g, X, np.linalg.cholesky(Om), M, 1)
+    n = 13
+    ne = O.pcg_ne(X, Om, Y, tol=1e-10, maxit=10 * n)
+    aug = O.sur_pcg_aug(X, Om, Y, tol=1e-10, stag_window=1000)
+    assert aug["status"] == [O.STATUS_CONVERGED] and aug["iters"][0] < n + 10
+    assert ne["iters"][0] > 3 * n, ne["iters"]
+    cut = O.pcg_ne(X, Om, Y, tol=1e-10, maxit=n)
+    bg = O.gls_formula(X, Om, Y)
+    assert rel(cut["b"], bg) > 0.5
