@@ -195,6 +195,31 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
                                         double* relres, glm_sur_stream_t stream);
 
 /*
+ * glm_sur_solve_ne -- PCG-NE, the comparator of the paper's Monte-Carlo study
+ * (Sec. "Statistical properties of the PCG-Aug estimator") and experiments
+ * (Sec. "Experimental Tests"): the conjugate gradient method of Algorithm pcg
+ * with K = I on the normal equations (X^T Sigma^-1 X) beta = X^T Sigma^-1 y,
+ * beta_1 = 0, in float64 whatever opts.precision says.  X = (+) Q_i R_i is
+ * applied through the setup factors and Sigma^-1 = Omega^-1 (x) I_M, with
+ * Omega^-1 from a Cholesky factorisation of the handle's Omega (the
+ * preconditioner block opts.precond does not apply: PCG-NE has none).  A
+ * column stops when ||f_i|| <= opts.tol ||f_1|| (f = A beta - h, the
+ * gradient of Algorithm pcg) with status GLM_SUR_OK, or after opts.maxit
+ * steps (0: 4 n) with GLM_SUR_NOT_CONVERGED; a non-positive p^T A p gives
+ * GLM_SUR_BREAKDOWN.  In exact arithmetic it ends within n steps; on an
+ * ill-conditioned X^T Sigma^-1 X it needs many more (the paper's point).
+ * Arguments as glm_sur_solve; iters and relres (= ||f|| / ||f_1||) per
+ * column; glm_sur_get_status reports the columns.  Row-reduced handles
+ * (opts.reduce_rows) run it on the reduced model.
+ * GLM_SUR_INVALID_ARG: Omega not numerically positive definite (a pivot of
+ * its Cholesky factorisation below 1e-13 of its largest diagonal entry; the
+ * normal equations need Sigma^-1), a handle with restrictions, or bad sizes.
+ * glm_sur_get_w and glm_sur_backward are refused until the next glm_sur_solve.
+ */
+glm_sur_status glm_sur_solve_ne(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb,
+                                int* iters, double* relres, glm_sur_stream_t stream);
+
+/*
  * glm_sur_backward -- adjoint of the last glm_sur_solve for a loss L(b).
  * K = [[Sigma, X], [X^T, 0]] of eq. (aug1) is symmetric, so with
  * (lam; mu) = K^-1 (0; dL/db):  dL/dy = lam  and  dL/dK = -(lam; mu)(w; b)^T,

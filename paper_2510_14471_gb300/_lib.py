@@ -58,6 +58,7 @@ SIGNATURES = {
     "glm_sur_get_status": (_I, [_VP, ctypes.POINTER(_I), _I]),
     "glm_sur_set_restrictions": (_I, [_VP, _VP, _I64, _I, _VP]),
     "glm_sur_solve_restricted": (_I, [_VP, _VP, _I64, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
+    "glm_sur_solve_ne": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_backward": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_get_w": (_I, [_VP, _VP, _I64, _VP]),
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
@@ -144,6 +145,11 @@ def glm_sur_solve(h: int, Y_ptr: int, ldy: int, k: int, b_ptr: int, ldb: int, it
 
 def glm_sur_set_restrictions(h: int, C_ptr: int, ldc: int, kc: int, stream: int) -> None:
     check(lib().glm_sur_set_restrictions(h, C_ptr, ldc, kc, stream), "glm_sur_set_restrictions")
+
+
+def glm_sur_solve_ne(h: int, Y_ptr: int, ldy: int, k: int, b_ptr: int, ldb: int, iters_ptr: int,
+                     relres_ptr: int, stream: int = 0) -> None:
+    check(lib().glm_sur_solve_ne(h, Y_ptr, ldy, k, b_ptr, ldb, iters_ptr, relres_ptr, stream), "glm_sur_solve_ne")
 
 
 def glm_sur_solve_restricted(h: int, Y_ptr: int, ldy: int, d_ptr: int, ldd: int, k: int, b_ptr: int, ldb: int,

@@ -16,6 +16,7 @@
 #include "adjoint.h"
 #include "glm_sur.h"
 #include "internal.h"
+#include "ne.h"
 #include "noalloc.h"
 #include "pcg.h"
 #include "reduce.h"
@@ -123,6 +124,12 @@ struct glm_sur_ctx {
   double* opart = nullptr;     // chunk partials of the Omega gradient
   int acap = 0;                // k capacity of wfwd / lam1
   int64_t ocap = 0;            // doubles in opart
+  // PCG-NE comparator (glm_sur_solve_ne)
+  double* ne_buf = nullptr;    // beta, f, p, q (n x k each), cvec (n' x k), c, c1, relres (k each)
+  int* ne_ibuf = nullptr;      // active, iters, status (k each)
+  double* ne_om = nullptr;     // Omega^-1 (G x Gq), then the Cholesky factor and its inverse (G x G each)
+  int* ne_hact = nullptr;      // pinned copy of the active flags
+  int necap = 0;
 };
 
 namespace {
@@ -1133,9 +1140,134 @@ glm_sur_status ensure_adjoint_workspace(glm_sur_ctx* h, int k, int nch) {
   return GLM_SUR_OK;
 }
 
+glm_sur_status ensure_ne_workspace(glm_sur_ctx* h, int k) {
+  const Geom& gm = h->gm;
+  if (!h->ne_om) {
+    GS_CUDA_TRY(dalloc(&h->ne_om, (size_t)gm.G * gm.Gq + 2 * (size_t)gm.G * gm.G));
+    GS_CUDA_TRY(cudaMallocHost(&h->ne_hact, kMaxRhs * sizeof(int)));
+  }
+  if (k > h->necap) {
+    dfree(h->ne_buf);
+    dfree(h->ne_ibuf);
+    h->necap = 0;
+    GS_CUDA_TRY(dalloc(&h->ne_buf, (size_t)k * (4 * (size_t)gm.n + gm.np + 3)));
+    GS_CUDA_TRY(dalloc(&h->ne_ibuf, (size_t)3 * k));
+    h->necap = k;
+  }
+  return GLM_SUR_OK;
+}
+
+// PCG-NE (the comparator of Sec. "Statistical properties of the PCG-Aug
+// estimator" and Sec. "Experimental Tests"): Algorithm pcg with K = I on
+// (X^T Sigma^-1 X) beta = X^T Sigma^-1 y, beta_1 = 0, float64.  A beta =
+// R^T Q^T Sigma^-1 Q R beta with Sigma^-1 = Omega^-1 (x) I_M; Omega^-1 =
+// L^-T L^-1 from the Cholesky factor of the given Omega (the preconditioner
+// block of the PCG-Aug solves plays no part).  Stops per column when
+// ||f|| <= tol ||f_1|| or after maxit steps (opts.maxit, 0: 4 n).
+glm_sur_status ne_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
+                        double* relres, cudaStream_t s) {
+  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  if (h->sub) {
+    if (k < 1 || k > kMaxRhs || ldy < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
+    glm_sur_status rc = rotate_in(h, Y, ldy, k, s);
+    if (rc != GLM_SUR_OK) return rc;
+    return ne_solve(h->sub, h->yred, (int64_t)h->gm.G * h->gm.n, k, b, ldb, iters, relres, s);
+  }
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G, mk = m * k;
+  if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n || h->kc > 0) return GLM_SUR_INVALID_ARG;
+  IterPlan p64;
+  glm_sur_status rc = prepare_solve(h, k, p64);
+  if (rc != GLM_SUR_OK) return rc;
+  rc = ensure_ne_workspace(h, k);
+  if (rc != GLM_SUR_OK) return rc;
+  h->has_w = false;
+  h->last_k = k;
+  const int G = gm.G;
+  double* Oinv = h->ne_om;
+  double* Lw = Oinv + (size_t)G * gm.Gq;
+  double* Linv = Lw + (size_t)G * G;
+  // Omega^-1 (positive definite Omega only: the normal equations need Sigma^-1)
+  GS_CUDA_TRY(cudaMemcpy2DAsync(Lw, G * sizeof(double), h->Omraw, gm.Gq * sizeof(double), G * sizeof(double), G,
+                                cudaMemcpyDeviceToDevice, s));
+  GS_CUDA_TRY(cudaMemsetAsync(h->setup_flags, 0, sizeof(int), s));
+  GS_CUDA_TRY(cholesky_lower(G, Lw, h->setup_flags, 1e-13, s));
+  int flag = 0;
+  GS_CUDA_TRY(cudaMemcpyAsync(&flag, h->setup_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flag) return GLM_SUR_INVALID_ARG;
+  GS_CUDA_TRY(launch_tri_inverse(G, Lw, Linv, s));
+  GS_CUDA_TRY(cudaMemsetAsync(Oinv, 0, sizeof(double) * (size_t)G * gm.Gq, s));
+  launch_dgemm(G, G, G, Linv, 1, G, Linv, G, 1, Oinv, gm.Gq, 1, s);
+  // state
+  NeState st;
+  st.k = k;
+  st.tol = h->opts.tol;
+  st.maxit = h->opts.maxit > 0 ? h->opts.maxit : 4 * gm.n;
+  const size_t nk = (size_t)gm.n * k;
+  st.beta = h->ne_buf;
+  st.f = st.beta + nk;
+  st.p = st.f + nk;
+  st.q = st.p + nk;
+  double* cvec = st.q + nk;
+  st.c = cvec + (size_t)gm.np * k;
+  st.c1 = st.c + k;
+  st.relres = st.c1 + k;
+  st.active = h->ne_ibuf;
+  st.iters = st.active + k;
+  st.status = st.iters + k;
+  GS_CUDA_TRY(cudaMemsetAsync(cvec, 0, sizeof(double) * (size_t)gm.np * k, s));
+  GS_CUDA_TRY(cudaMemsetAsync(h->st.err, 0, sizeof(int), s));
+  double* Cpart = reinterpret_cast<double*>(h->Cpart);
+  double* zero = h->u64;        // m x k zeros: S of the update and Y of the residual kernel
+  GS_CUDA_TRY(cudaMemsetAsync(zero, 0, mk * sizeof(double), s));
+  launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s);
+  // h = X^T Sigma^-1 y:  E = 0 - y Omega^-1,  C = Q^T E,  h = -[R_i^T C_i]
+  launch_sigma_resid<double>(p64, gm, k, Oinv, zero, h->y64, h->E64, s);
+  launch_proj_partial<double>(p64, gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+  launch_reduce<double>(p64, gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  launch_ne_step(gm, k, h->R, h->C64, st, 1, s);
+  h->launches += 7;
+  GS_CUDA_TRY(cudaGetLastError());
+  const int chunk = std::max(1, h->opts.chunk);
+  for (int it = 0; it < st.maxit;) {
+    const int steps = std::min(chunk, st.maxit - it);
+    for (int c = 0; c < steps; ++c) {
+      // v = Q (R p)  (update kernel: g = 0 g - 1 (0 - Q c))
+      launch_ne_rmul(gm, k, h->R, st.p, cvec, s);
+      launch_proj_update<double>(p64, gm, k, h->Q64, zero, h->g64, cvec, 0, nullptr, 1.0, h->cpart, h->st, 0, s);
+      // E = -Sigma^-1 v;  C = Q^T E;  q = -[R_i^T C_i] = A p, then the CG step
+      launch_sigma_resid<double>(p64, gm, k, Oinv, zero, h->g64, h->E64, s);
+      launch_proj_partial<double>(p64, gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+      launch_reduce<double>(p64, gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+      launch_ne_step(gm, k, h->R, h->C64, st, 0, s);
+    }
+    h->launches += 6 * steps;
+    GS_CUDA_TRY(cudaGetLastError());
+    it += steps;
+    GS_CUDA_TRY(cudaMemcpyAsync(h->ne_hact, st.active, k * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA_TRY(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < k; ++j) any |= h->ne_hact[j] != 0;
+    if (!any) break;
+  }
+  launch_ne_store(gm, k, st.beta, b, ldb, s);
+  h->launches += 1;
+  GS_CUDA_TRY(cudaMemcpyAsync(h->d_status_final, st.status, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, st.iters, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (relres) GS_CUDA_TRY(cudaMemcpyAsync(relres, st.relres, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  GS_CUDA_TRY(cudaGetLastError());
+  return GLM_SUR_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+glm_sur_status glm_sur_solve_ne(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb,
+                                int* iters, double* relres, glm_sur_stream_t stream) {
+  return ne_solve(h, Y, ldy, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
+}
 
 glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
                              double* relres, glm_sur_stream_t stream) {
@@ -1401,6 +1533,8 @@ void glm_sur_destroy(glm_sur_t h) {
   dfree(h->gm.d_ug_blk0); dfree(h->gm.d_col_blk);
   dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
   dfree(h->wfwd); dfree(h->lam1); dfree(h->opart);
+  dfree(h->ne_buf); dfree(h->ne_ibuf); dfree(h->ne_om);
+  if (h->ne_hact) cudaFreeHost(h->ne_hact);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);

@@ -116,6 +116,23 @@ class GlmSur:
         self.generation += 1
         return SolveResult(b.t(), iters, relres, status)
 
+    def solve_ne(self, Y) -> SolveResult:
+        """PCG-NE: conjugate gradients on X^T Sigma^-1 X beta = X^T Sigma^-1 y
+        (float64, positive definite Omega).  Y as in ``solve``; b as (n, k)."""
+        Y = _dev_f64(Y, self.device)
+        if Y.dim() == 1:
+            Y = Y[:, None]
+        m, k = Y.shape
+        Ycm = Y.t().contiguous()
+        b = torch.empty((k, self.n), dtype=torch.float64, device=self.device)
+        iters = torch.zeros(k, dtype=torch.int32, device=self.device)
+        relres = torch.zeros(k, dtype=torch.float64, device=self.device)
+        L.glm_sur_solve_ne(self._h, Ycm.data_ptr(), m, k, b.data_ptr(), self.n, iters.data_ptr(),
+                           relres.data_ptr(), self._stream())
+        status = L.glm_sur_get_status(self._h, k)
+        self.generation += 1
+        return SolveResult(b.t(), iters, relres, status)
+
     def backward(self, dL_db, want_y: bool = True, want_omega: bool = True):
         """Adjoint of the last solve (same k, no restrictions, Omega unchanged).
         dL_db: (n, k) or (n,).  Returns (dL_dY (m, k) or None, dL_dOmega (G, G)

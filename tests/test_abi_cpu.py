@@ -61,6 +61,7 @@ def test_host_only_calls(libpath):
     assert L.glm_sur_backward(None, 1, 1, 1, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_solve_restricted(None, 1, 1, None, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_set_restrictions(None, 1, 1, 1, None) == _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_solve_ne(None, 1, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
     bh = ctypes.c_void_p()
     g1 = (ctypes.c_int * 1)(2)
     m1 = (ctypes.c_int * 1)(100)
