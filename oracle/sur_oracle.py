@@ -25,6 +25,11 @@ of General Linear Models"):
   * ``sur_pcg_aug3``      -- Algorithm glmpcg3 (s-recurrence), fixed steps.
   * ``pcg_ne``            -- the PCG-NE comparator: CG on the normal equations
                              with Sigma^-1 = Omega^-1 (x) I_M (PD Omega).
+  * ``pcg_aug_reduced``   -- Algorithm glmpcg2 in the reduced form of
+                             eq. (urwProj) (null-space PCG, no v_i).
+  * ``mvrglm_pcg_aug``    -- MVRGLM: model reduction by QR of Z0, updating
+                             QRDs [R0; C_i] = Qt_i R_i, Algorithm glmpcg2 with
+                             the block-diagonal X* and Pi.
   * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
                              Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
   * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
@@ -48,7 +53,8 @@ __all__ = [
     "sur_dense", "augmented_matrix", "aug_dense_solve", "gls_formula", "aug_lemma",
     "ols_blocks", "sur_gls_structured", "pcg", "sur_pcg_aug", "rglm_pcg_aug",
     "sur_gls_gradient", "sur_gls_gradient_kron", "sur_gls_refined", "augmented_residual", "lse_solve",
-    "sur_pcg_aug3", "jacobi_delta", "scaled_identity_delta", "pcg_ne",
+    "sur_pcg_aug3", "jacobi_delta", "scaled_identity_delta", "pcg_ne", "MvOps", "mvrglm_pcg_aug",
+    "pcg_aug_reduced",
 ]
 
 
@@ -293,6 +299,7 @@ class SurOps:
         self.offs = np.cumsum([0] + self.n_i)
         self.QR = [np.linalg.qr(Xi) for Xi in X_blocks]
         self.delta = np.ones(self.G) if delta is None else np.asarray(delta, dtype=float)
+        self.m = self.G * self.M
 
     def sigma(self, u):
         # (U Omega)_h = sum_g U_g omega_gh: with the G columns of every U_j as
@@ -364,7 +371,7 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     z_hat = X*^T (y - Sigma w) (step 10 of the algorithm).
     Returns dict(b, w, iters, status, relres[, history])."""
     op = ops if ops is not None else SurOps(X_blocks, Omega, delta)
-    m = op.G * op.M
+    m = op.m
     Y = np.asarray(Y, dtype=float).reshape(m, -1)
     k = Y.shape[1]
     n = int(op.offs[-1])
@@ -435,6 +442,89 @@ def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
     return out
 
 
+def pcg_aug_reduced(ops, Y, tol=1e-13, maxit=None, stag_window=25, record=False):
+    """Algorithm glmpcg2 in the reduced form of eq. (urwProj): with r_i, u_i,
+    w_i split on range(X) and null(X^T), the null-space parts follow PCG on
+    A w~ = Q_N^T y (A = Q_N^T Sigma Q_N, preconditioner B^-1, B = Q_N^T D Q_N)
+    and the directions v_i are not needed.  In the full space, with D
+    commuting with P (block i of D equal to delta_i I), this reads
+      g_1 = P r_1 = -P y,  u_1 = D^-1 g_1,  c_1 = g_1^T D^-1 g_1,
+      d_i = u_i^T Sigma u_i,  lambda_i = c_i / d_i,  w_{i+1} = w_i - lambda_i u_i,
+      g_{i+1} = g_i - lambda_i P Sigma u_i,  c_{i+1} = g_{i+1}^T D^-1 g_{i+1},
+      u_{i+1} = D^-1 g_{i+1} + (c_{i+1} / c_i) u_i,
+    and b = X*^T (y - Sigma w) at the end (step 10).  Unlike the literal
+    recursion r_{i+1} = r_i - lambda_i (Sigma u_i + X v_i), nothing here
+    grows with the range-space part z_i of the iterate, which is multiplied
+    by about (1 - lambda_i) per step: when lambda_i >> 1 (a Sigma whose
+    Rayleigh quotients on null(X^T) are far below those of D, as with the
+    zero-variance restriction rows) that recursion loses P r to rounding.
+    Stopping rules as ``sur_pcg_aug``.  ``ops`` provides m, offs, sigma,
+    proj, dinv and xstar_t.  Returns dict(b, w, iters, status, relres[, history])."""
+    op = ops
+    m = op.m
+    Y = np.asarray(Y, dtype=float).reshape(m, -1)
+    k = Y.shape[1]
+    n = int(op.offs[-1])
+    if maxit is None:
+        maxit = m - n + 1
+    w = np.zeros((m, k))
+    g = -op.proj(Y)
+    Dg = op.dinv(g)
+    c = np.sum(g * Dg, axis=0)
+    u = Dg.copy()
+    c1 = c.copy()
+    active = c1 > 0
+    iters = np.zeros(k, dtype=int)
+    status = np.array([STATUS_CONVERGED if not a else STATUS_NOT_CONVERGED for a in active], dtype=object)
+    relres = np.where(c1 > 0, 1.0, 0.0)
+    cbest = c.copy()
+    itbest = np.zeros(k, dtype=int)
+    hist = {"w": [w.copy()], "c": [c.copy()]} if record else None
+    for it in range(1, maxit + 1):
+        if not active.any():
+            break
+        Su = op.sigma(u)
+        dd = np.sum(u * Su, axis=0)
+        bad = active & (~np.isfinite(dd) | (dd <= 0))
+        for j in np.where(bad)[0]:
+            status[j] = STATUS_BREAKDOWN
+        active &= ~bad
+        lam = np.where(active, c / np.where(active, dd, 1.0), 0.0)
+        w = w - lam * u
+        g = g - lam * op.proj(Su)
+        Dg = op.dinv(g)
+        c_new = np.where(active, np.sum(g * Dg, axis=0), c)
+        iters = iters + active
+        rr = np.sqrt(np.maximum(c_new, 0.0) / np.where(c1 > 0, c1, 1.0))
+        relres = np.where(active, rr, relres)
+        bad_c = active & (~np.isfinite(c_new) | (c_new < 0))
+        for j in np.where(bad_c)[0]:
+            status[j] = STATUS_BREAKDOWN
+        active &= ~bad_c
+        conv = active & (rr <= tol)
+        for j in np.where(conv)[0]:
+            status[j] = STATUS_CONVERGED
+        active &= ~conv
+        better = active & (c_new < cbest)
+        cbest = np.where(better, c_new, cbest)
+        itbest = np.where(better, it, itbest)
+        stag = active & (it - itbest >= stag_window)
+        for j in np.where(stag)[0]:
+            status[j] = STATUS_STAGNATED
+        active &= ~stag
+        mu = np.where(active, c_new / np.where(c > 0, c, 1.0), 0.0)
+        u = np.where(active, Dg + mu * u, u)
+        c = np.where(active, c_new, c)
+        if record:
+            hist["w"].append(w.copy())
+            hist["c"].append(c_new.copy())
+    b = op.xstar_t(Y - op.sigma(w))
+    out = dict(b=b, w=w, iters=iters, status=list(status), relres=relres)
+    if record:
+        out["history"] = hist
+    return out
+
+
 def sur_pcg_aug3(X_blocks, Omega, Y, iters, delta=None, ops=None):
     """Algorithm glmpcg3 (the alternative PCG-Aug) in the SUR form, for a
     fixed number of steps and without stop tests (its iterates are compared
@@ -444,7 +534,7 @@ def sur_pcg_aug3(X_blocks, Omega, Y, iters, delta=None, ops=None):
     r_{i+1} = r_i - lambda_i (Sigma Pi + X X*^T) s_i.  Start w_1 = 0, z_1 = 0.
     Returns dict(b, w, history: list of w iterates and of c)."""
     op = ops if ops is not None else SurOps(X_blocks, Omega, delta)
-    m = op.G * op.M
+    m = op.m
     Y = np.asarray(Y, dtype=float).reshape(m, -1)
     k = Y.shape[1]
     w = np.zeros((m, k))
@@ -639,6 +729,111 @@ def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=25
         c = np.where(active, c_new, c)
     b = xstar_t(yaug - sigma(w))
     return dict(b=b, w=w, iters=iters, status=status, relres=relres)
+
+
+# ----------------------------------------------------------------------------
+# restricted multivariate GLM (MVRGLM)
+# ----------------------------------------------------------------------------
+
+class MvOps:
+    """The applies of the restricted multivariate GLM after model reduction
+    (Sec. "Multivariate linear models with parameters restrictions"):
+    Y = Z0 B + U with rows of U iid (0, Omega0) and restrictions C_i b_i =
+    gamma_i on each column b_i of B (no cross-equation restrictions).  With
+    Z0 = Q0 R0 the reduced model has Z = I_G (x) R0, Omega = Omega0 (x) I_N;
+    eq. (RGLM1setup) adds the k_i restriction rows of each equation with zero
+    variance.  Ordered equation by equation (the row permutation under which
+    X* and Pi are block diagonal), equation i holds the N + k_i rows
+    [R0; C_i], and the updating QRD [R0; C_i] = Qt_i R_i (eq. MvRGLMQRi) gives
+      X*  = (+)_i Qt_i R_i^-T,     P = (+)_i (I - Qt_i Qt_i^T),
+      Sigma u: rows 0..N-1 of equation h get sum_g omega_gh u_g[0..N-1],
+               the restriction rows get 0.
+    The preconditioner block is D = D_Z (+) D_C with D_Z = D0 (x) I_N and
+    D_C = D0 on the restriction rows of each equation (delta_i on every row
+    of equation i), so Pi = P D^-1 and the delta_i cancel in X*."""
+
+    def __init__(self, R0, C_list, Omega0, delta=None):
+        self.R0 = np.asarray(R0, dtype=float)
+        self.N = self.R0.shape[0]
+        self.G = len(C_list)
+        self.C = [np.asarray(c, dtype=float).reshape(-1, self.N) for c in C_list]
+        self.k_i = [c.shape[0] for c in self.C]
+        self.rows = [self.N + ki for ki in self.k_i]
+        self.roff = np.cumsum([0] + self.rows)
+        self.m = int(self.roff[-1])
+        self.offs = self.N * np.arange(self.G + 1)
+        self.Xt = [np.vstack([self.R0, c]) for c in self.C]
+        self.QR = [np.linalg.qr(x) for x in self.Xt]           # eq. (MvRGLMQRi)
+        self.Omega = np.asarray(Omega0, dtype=float)
+        self.delta = np.ones(self.G) if delta is None else np.asarray(delta, dtype=float)
+
+    def _blk(self, v, i):
+        return v[self.roff[i]:self.roff[i + 1]]
+
+    def sigma(self, u):
+        N = self.N
+        out = np.zeros_like(u)
+        U0 = np.stack([self._blk(u, i)[:N] for i in range(self.G)])      # (G, N, k)
+        S0 = np.tensordot(self.Omega.T, U0, axes=1)                      # (G, N, k)
+        for h in range(self.G):
+            out[self.roff[h]:self.roff[h] + N] = S0[h]
+        return out
+
+    def proj(self, xi):
+        out = np.empty_like(xi)
+        for i, (Qi, _) in enumerate(self.QR):
+            b = self._blk(xi, i)
+            out[self.roff[i]:self.roff[i + 1]] = b - Qi @ (Qi.T @ b)
+        return out
+
+    def dinv(self, xi):
+        return xi / np.repeat(self.delta, self.rows)[:, None]
+
+    def pi(self, xi):
+        return self.dinv(self.proj(xi))
+
+    def xstar_t(self, xi):
+        return np.vstack([np.linalg.solve(Ri, Qi.T @ self._blk(xi, i)) for i, (Qi, Ri) in enumerate(self.QR)])
+
+    def xmul(self, v):
+        return np.vstack([self.Xt[i] @ v[self.offs[i]:self.offs[i + 1]] for i in range(self.G)])
+
+
+def mvrglm_pcg_aug(Z0, Y, Omega0, C_list, gamma_list=None, tol=1e-13, maxit=None, stag_window=25,
+                   delta=None, record=False):
+    """MVRGLM: the restricted multivariate GLM estimated by model reduction
+    (QR of Z0, Y0 = Q0^T Y) and Algorithm glmpcg2, in the reduced form of
+    eq. (urwProj) (``pcg_aug_reduced``: the zero-variance restriction rows
+    make lambda_i >> 1, where the literal r-recursion is unstable), with the
+    block-diagonal applies of ``MvOps``; at most sum_i k_i + 1 steps in exact
+    arithmetic (m + k - n + 1 with m = n = G N).  Y: (M, G) or (M, G, k); gamma_i:
+    (k_i,) or (k_i, k), zero when not given.  Returns dict(B (N, G, k), b
+    (G N, k) = vec(B), iters, status, relres[, history])."""
+    Z0 = np.asarray(Z0, dtype=float)
+    Y = np.asarray(Y, dtype=float)
+    if Y.ndim == 2:
+        Y = Y[:, :, None]
+    M, G, k = Y.shape
+    Q0, R0 = np.linalg.qr(Z0)                                # model reduction
+    Y0 = np.tensordot(Q0.T, Y, axes=1)                        # (N, G, k)
+    ops = MvOps(R0, C_list, Omega0, delta)
+    parts = []
+    for i in range(G):
+        gi = np.zeros((ops.k_i[i], k))
+        if gamma_list is not None and ops.k_i[i] > 0:
+            gi = gi + np.asarray(gamma_list[i], dtype=float).reshape(ops.k_i[i], -1)
+        parts.append(np.vstack([Y0[:, i, :], gi]))
+    yaug = np.vstack(parts)
+    if maxit is None:
+        # the bound sum k_i + 1 holds in exact arithmetic; rounding costs a
+        # few more steps on ill-conditioned restriction systems
+        maxit = 2 * (sum(ops.k_i) + 1) + 10
+    res = pcg_aug_reduced(ops, yaug, tol=tol, maxit=maxit, stag_window=stag_window, record=record)
+    N = ops.N
+    res["B"] = res["b"].reshape(G, N, k).transpose(1, 0, 2)
+    res["ops"] = ops
+    res["yaug"] = yaug
+    return res
 
 
 # ----------------------------------------------------------------------------
