@@ -195,6 +195,43 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
                                         double* relres, glm_sur_stream_t stream);
 
 /*
+ * glm_sur_mvrglm_setup -- the restricted multivariate GLM of Sec.
+ * "Multivariate linear models with parameters restrictions" (MVRGLM):
+ * Y = Z0 B + U (Y, U: M x G; B: N x G), vec(U) ~ (0, Omega0 (x) I_M), with
+ * k_i linear restrictions C_i b_i = gamma_i on column i of B (no
+ * cross-equation restrictions).  Setup factors Z0 = Q0 R0 (model reduction,
+ * M rows -> N) and, for every equation, the updating QRD [R0; C_i] =
+ * Qt_i R_i (eq. MvRGLMQRi); each step of Algorithm glmpcg2 then applies
+ * Qt_i, Qt_i^T and R_i^-T with Sigma = Omega0 (x) I_N on the reduced rows and
+ * 0 on the restriction rows (eq. RGLM1setup).  At most sum_i k_i + 1 steps in
+ * exact arithmetic (m + k - n + 1 with m = n = G N).
+ *   Z0     : DEVICE, M x N column-major, ldz >= M; full column rank
+ *            (GLM_SUR_RANK_DEFICIENT otherwise, GLM_SUR_NONFINITE for a
+ *            NaN / Inf entry).  1 <= N <= 64, M >= N.
+ *   Omega0 : DEVICE, G x G (symmetric; positive definite on the null space
+ *            of the restricted regressors).
+ *   k_i    : HOST, G counts, 0 <= k_i <= N.
+ *   C      : DEVICE, (sum k_i) x N column-major, ldc >= sum k_i: rows
+ *            k_1 + ... + k_{i-1} .. + k_i - 1 hold C_i (full row rank each);
+ *            NULL when every k_i is 0.
+ *   opts   : as glm_sur_setup (reduce_rows is ignored: the model reduction
+ *            is always applied); precond D0 = alpha I or diag(Omega0) scales
+ *            every row of equation i, the restriction rows included (D_C of
+ *            eq. (3) = delta_i I).
+ * Solves: glm_sur_solve (gamma = 0, e.g. exclusion restrictions) and
+ * glm_sur_solve_restricted with d = gamma ((sum k_i) x k column-major, ldd >=
+ * sum k_i), Y in the layout of glm_sur_solve (column j = vec(Y_j), ldy >=
+ * G M), b = vec(B) (G N x k, ldb >= G N).  glm_sur_set_omega,
+ * glm_sur_set_opts and glm_sur_get_status apply; glm_sur_backward,
+ * glm_sur_solve_ne, glm_sur_set_restrictions, glm_sur_get_w and
+ * glm_sur_get_factors return GLM_SUR_INVALID_ARG.  Release with
+ * glm_sur_destroy.
+ */
+glm_sur_status glm_sur_mvrglm_setup(glm_sur_t* out, int G, int64_t M, int N, const double* Z0, int64_t ldz,
+                                    const double* Omega0, const int* k_i, const double* C, int64_t ldc,
+                                    const glm_sur_opts* opts, glm_sur_stream_t stream);
+
+/*
  * glm_sur_solve_ne -- PCG-NE, the comparator of the paper's Monte-Carlo study
  * (Sec. "Statistical properties of the PCG-Aug estimator") and experiments
  * (Sec. "Experimental Tests"): the conjugate gradient method of Algorithm pcg

@@ -59,6 +59,7 @@ SIGNATURES = {
     "glm_sur_set_restrictions": (_I, [_VP, _VP, _I64, _I, _VP]),
     "glm_sur_solve_restricted": (_I, [_VP, _VP, _I64, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_solve_ne": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _VP, _VP]),
+    "glm_sur_mvrglm_setup": (_I, [_VP, _I, _I64, _I, _VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP]),
     "glm_sur_backward": (_I, [_VP, _VP, _I64, _I, _VP, _I64, _VP, _I64, _VP, _VP, _VP]),
     "glm_sur_get_w": (_I, [_VP, _VP, _I64, _VP]),
     "glm_sur_get_factors": (_I, [_VP, _VP, _I64, _VP, _VP]),
@@ -123,6 +124,16 @@ def glm_sur_setup(G: int, M: int, n_i, X_ptr: int, ldx: int, Omega_ptr: int, opt
     rc = lib().glm_sur_setup(ctypes.byref(h), G, M, arr, X_ptr, ldx, Omega_ptr,
                              ctypes.byref(opts) if opts is not None else None, stream)
     check(rc, "glm_sur_setup")
+    return h.value
+
+
+def glm_sur_mvrglm_setup(G: int, M: int, N: int, Z0_ptr: int, ldz: int, Omega0_ptr: int, k_i, C_ptr: int,
+                         ldc: int, opts: GlmSurOpts | None, stream: int) -> int:
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * G)(*[int(v) for v in k_i])
+    rc = lib().glm_sur_mvrglm_setup(ctypes.byref(h), G, M, N, Z0_ptr, ldz, Omega0_ptr, arr, C_ptr, ldc,
+                                    ctypes.byref(opts) if opts is not None else None, stream)
+    check(rc, "glm_sur_mvrglm_setup")
     return h.value
 
 

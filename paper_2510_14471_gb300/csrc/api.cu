@@ -16,6 +16,7 @@
 #include "adjoint.h"
 #include "glm_sur.h"
 #include "internal.h"
+#include "mvrglm.h"
 #include "ne.h"
 #include "noalloc.h"
 #include "pcg.h"
@@ -130,6 +131,14 @@ struct glm_sur_ctx {
   double* ne_om = nullptr;     // Omega^-1 (G x Gq), then the Cholesky factor and its inverse (G x G each)
   int* ne_hact = nullptr;      // pinned copy of the active flags
   int necap = 0;
+  // restricted multivariate GLM (glm_sur_mvrglm_setup): the solves run on
+  // `sub`, the G equations [R0; C_i] (N + kmax rows each) with Sigma = 0 on
+  // the restriction rows
+  int mv_N = 0, mv_kmax = 0, mv_ktot = 0;
+  int* mv_koff = nullptr;      // device, G + 1: first restriction row of each equation
+  double* mv_Q0 = nullptr;     // M x N row-major, Z0 = Q0 R0
+  double* mv_y = nullptr;      // assembled responses, (G (N + kmax)) x k column-major
+  int64_t mv_ycap = 0;
 };
 
 namespace {
@@ -260,7 +269,7 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
     }
     p.extra_cpart = h->kc > 0 ? 1 : 0;
     // fused float32 step with the tensor-core Sigma-apply (pcg_tc.cu)
-    if (!is_double && h->kc == 0 && h->opts.step_kernels != GLM_SUR_STEP_SIMT &&
+    if (!is_double && h->kc == 0 && gm.Ms == gm.M && h->opts.step_kernels != GLM_SUR_STEP_SIMT &&
         tc_step_eligible(gm.G, k, gm.np, nmax)) {
       p.tc_gp = gm.G <= 32 ? 32 : 64;
       const int TV = 128 / k;
@@ -666,6 +675,7 @@ glm_sur_status setup_reduced(glm_sur_t* out, int G, int64_t M, const int* n_i, i
   h->gm.G = G;
   h->gm.Gq = round_up4(G);
   h->gm.M = M;
+  h->gm.Ms = M;
   h->gm.n = n;
   h->n_i.assign(n_i, n_i + G);
   h->launches = 11;
@@ -793,6 +803,7 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
   gm.G = G;
   gm.Gq = round_up4(G);
   gm.M = M;
+  gm.Ms = M;
   h->n_i.assign(n_i, n_i + G);
   h->off.assign(G + 1, 0);
   h->poff.assign(G + 1, 0);
@@ -891,6 +902,114 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i, c
     return bail(rc);
   }
 #undef SETUP_TRY
+  return GLM_SUR_OK;
+}
+
+glm_sur_status glm_sur_mvrglm_setup(glm_sur_t* out, int G, int64_t M, int N, const double* Z0, int64_t ldz,
+                                    const double* Omega0, const int* k_i, const double* C, int64_t ldc,
+                                    const glm_sur_opts* opts, glm_sur_stream_t stream) {
+  if (!out || !Z0 || !Omega0 || !k_i) return GLM_SUR_INVALID_ARG;
+  *out = nullptr;
+  if (G < 1 || G > kMaxG || N < 1 || N > kMaxBlockCols || M < N || ldz < M) return GLM_SUR_INVALID_ARG;
+  int kmax = 0, ktot = 0;
+  std::vector<int> koff(G + 1, 0);
+  for (int i = 0; i < G; ++i) {
+    if (k_i[i] < 0 || k_i[i] > N) return GLM_SUR_INVALID_ARG;   // at most N independent restrictions
+    kmax = std::max(kmax, k_i[i]);
+    ktot += k_i[i];
+    koff[i + 1] = ktot;
+  }
+  if (ktot > 0 && (!C || ldc < ktot)) return GLM_SUR_INVALID_ARG;
+  glm_sur_opts o;
+  glm_sur_default_opts(&o);
+  if (opts) o = *opts;
+  if (validate_opts(&o) != GLM_SUR_OK) return GLM_SUR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int Mp = N + kmax;
+  double *Q0 = nullptr, *R0 = nullptr, *Xt = nullptr;
+  int64_t* roff = nullptr;
+  int *flags = nullptr, *dkoff = nullptr;
+  auto release = [&]() {
+    dfree(R0); dfree(Xt); dfree(roff); dfree(flags);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_last_error(e, what, __FILE__, __LINE__);
+    release();
+    dfree(Q0);
+    dfree(dkoff);
+    return e == cudaErrorMemoryAllocation ? GLM_SUR_OOM : GLM_SUR_CUDA_ERROR;
+  };
+#define MV_TRY(expr)                       \
+  do {                                     \
+    cudaError_t e_ = (expr);               \
+    if (e_ != cudaSuccess) return fail(e_, #expr); \
+  } while (0)
+  MV_TRY(dalloc(&Q0, (size_t)M * N));
+  MV_TRY(dalloc(&R0, (size_t)N * N));
+  MV_TRY(dalloc(&Xt, (size_t)Mp * G * N));
+  MV_TRY(dalloc(&roff, 2));
+  MV_TRY(dalloc(&flags, 1));
+  MV_TRY(dalloc(&dkoff, G + 1));
+  const int64_t roff_h[2] = {0, (int64_t)N * N};
+  MV_TRY(cudaMemcpyAsync(roff, roff_h, sizeof(roff_h), cudaMemcpyHostToDevice, s));
+  MV_TRY(cudaMemcpyAsync(dkoff, koff.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  MV_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  MV_TRY(cudaMemsetAsync(Q0, 0, sizeof(double) * (size_t)M * N, s));
+  // model reduction: Householder TSQR of Z0 (Q0 row-major M x N, R0 row-major)
+  {
+    QrPlan plan;
+    std::vector<QrBlock> qb(1, QrBlock{N, M, 0, ldz, 0, (int64_t)N});
+    build_qr_plan(qb, plan);
+    glm_sur_status rc = run_qr(plan, Z0, roff, Q0, R0, flags, s);
+    if (rc != GLM_SUR_OK) {
+      release();
+      dfree(Q0);
+      dfree(dkoff);
+      return rc;
+    }
+  }
+  int hflag = 0;
+  MV_TRY(cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MV_TRY(cudaStreamSynchronize(s));
+  if (hflag) {
+    release();
+    dfree(Q0);
+    dfree(dkoff);
+    return (hflag & 2) ? GLM_SUR_NONFINITE : GLM_SUR_RANK_DEFICIENT;   // Z0 not finite / not of full column rank
+  }
+  // the G blocks [R0; C_i; 0] and their setup (the updating QRDs)
+  launch_mv_build_x(G, N, Mp, R0, C, ldc, dkoff, Xt, s);
+  MV_TRY(cudaGetLastError());
+  std::vector<int> n_i(G, N);
+  glm_sur_opts so = o;
+  so.reduce_rows = 0;
+  glm_sur_t sub = nullptr;
+  glm_sur_status rc = glm_sur_setup(&sub, G, Mp, n_i.data(), Xt, Mp, Omega0, &so, stream);
+  MV_TRY(cudaStreamSynchronize(s));
+  release();
+  if (rc != GLM_SUR_OK) {
+    dfree(Q0);
+    dfree(dkoff);
+    return rc;
+  }
+  sub->gm.Ms = N;                    // Sigma = 0 on the restriction rows
+  glm_sur_ctx* h = new glm_sur_ctx();
+  h->opts = o;
+  h->sub = sub;
+  h->mv_N = N;
+  h->mv_kmax = kmax;
+  h->mv_ktot = ktot;
+  h->mv_koff = dkoff;
+  h->mv_Q0 = Q0;
+  h->gm.G = G;
+  h->gm.Gq = round_up4(G);
+  h->gm.M = M;
+  h->gm.Ms = M;
+  h->gm.n = G * N;
+  h->n_i.assign(G, N);
+  h->launches = 3;
+  *out = h;
+#undef MV_TRY
   return GLM_SUR_OK;
 }
 
@@ -1090,8 +1209,48 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
 }
 
 glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
+                          int64_t ldb, int* iters, double* relres, cudaStream_t s);
+
+// MVRGLM solve: Y0 = Q0^T Y (model reduction), y' = [Y0_i; gamma_i; 0] per
+// equation, then the SUR iteration of the masked model; b = vec(B).
+glm_sur_status mv_solve(glm_sur_t h, const double* Y, int64_t ldy, const double* gamma, int64_t ldd, int k,
+                        double* b, int64_t ldb, int* iters, double* relres, cudaStream_t s) {
+  const int G = h->gm.G, N = h->mv_N, Mp = N + h->mv_kmax;
+  const int64_t M = h->gm.M;
+  if (k < 1 || k > kMaxRhs || ldy < M * G || ldb < (int64_t)G * N) return GLM_SUR_INVALID_ARG;
+  if (gamma && ldd < h->mv_ktot) return GLM_SUR_INVALID_ARG;
+  const int64_t need0 = (int64_t)N * G * k, need1 = (int64_t)G * Mp * k;
+  if (need0 > h->yred_cap) {
+    dfree(h->yred);
+    h->yred_cap = 0;
+    GS_CUDA_TRY(dalloc(&h->yred, (size_t)need0));
+    h->yred_cap = need0;
+  }
+  if (need1 > h->mv_ycap) {
+    dfree(h->mv_y);
+    h->mv_ycap = 0;
+    GS_CUDA_TRY(dalloc(&h->mv_y, (size_t)need1));
+    h->mv_ycap = need1;
+  }
+  // Y0(:, j G + i) = Q0^T y_ij  (Q0 row-major M x N)
+  if (ldy == M * G) {
+    launch_dgemm(N, G * k, M, h->mv_Q0, 1, N, Y, 1, M, h->yred, 1, N, s);
+    h->launches += 1;
+  } else {
+    for (int j = 0; j < k; ++j)
+      launch_dgemm(N, G, M, h->mv_Q0, 1, N, Y + (int64_t)j * ldy, 1, M, h->yred + (int64_t)j * G * N, 1, N, s);
+    h->launches += k;
+  }
+  launch_mv_assemble(G, N, Mp, k, h->yred, gamma, ldd, h->mv_koff, h->mv_y, s);
+  h->launches += 1;
+  GS_CUDA_TRY(cudaGetLastError());
+  return solve_impl(h->sub, h->mv_y, (int64_t)G * Mp, nullptr, 0, k, b, ldb, iters, relres, s);
+}
+
+glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
                           int64_t ldb, int* iters, double* relres, cudaStream_t s) {
   if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  if (h->mv_N) return mv_solve(h, Y, ldy, d, ldd, k, b, ldb, iters, relres, s);
   if (h->sub) {
     // Remark rem:reduction: the same estimate from the n rotated rows
     if (k < 1 || k > kMaxRhs || ldy < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
@@ -1166,7 +1325,7 @@ glm_sur_status ensure_ne_workspace(glm_sur_ctx* h, int k) {
 // ||f|| <= tol ||f_1|| or after maxit steps (opts.maxit, 0: 4 n).
 glm_sur_status ne_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, double* b, int64_t ldb, int* iters,
                         double* relres, cudaStream_t s) {
-  if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
+  if (!h || !Y || !b || h->mv_N) return GLM_SUR_INVALID_ARG;
   if (h->sub) {
     if (k < 1 || k > kMaxRhs || ldy < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
     glm_sur_status rc = rotate_in(h, Y, ldy, k, s);
@@ -1283,7 +1442,7 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
 
 glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY, int64_t ldy,
                                 double* dL_dOmega, int64_t ldo, int* iters, double* relres, glm_sur_stream_t stream) {
-  if (!h || !dL_db || (!dL_dY && !dL_dOmega)) return GLM_SUR_INVALID_ARG;
+  if (!h || !dL_db || (!dL_dY && !dL_dOmega) || h->mv_N) return GLM_SUR_INVALID_ARG;
   if (h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;
   if (h->sub) {
     // the adjoint of the reduced model; dL/dy = Q dL/dy' (the rows outside
@@ -1342,6 +1501,7 @@ glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, i
 }
 
 glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ldc, int kc, glm_sur_stream_t stream) {
+  if (h && h->mv_N) return GLM_SUR_INVALID_ARG;   // the restrictions are the model's own
   if (h && h->sub) return glm_sur_set_restrictions(h->sub, C, ldc, kc, stream);
   if (!h || kc < 0 || (kc > 0 && (!C || ldc < kc))) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1522,6 +1682,9 @@ void glm_sur_destroy(glm_sur_t h) {
     cudaDeviceSynchronize();
     dfree(h->Qw);
     dfree(h->yred);
+    dfree(h->mv_koff);
+    dfree(h->mv_Q0);
+    dfree(h->mv_y);
     delete h;
     return;
   }

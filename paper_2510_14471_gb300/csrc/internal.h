@@ -63,6 +63,8 @@ glm_sur_status run_qr(const QrPlan& plan, const double* X, const int64_t* d_r_of
 struct Geom {
   int G = 0, Gq = 0, n = 0, np = 0, nq = 0;   // nq = np / 4 column quads
   int64_t M = 0;
+  int64_t Ms = 0;            // rows t < Ms carry Sigma = Omega (x) I; Sigma = 0 on rows t >= Ms
+                             // (the restriction rows of the restricted multivariate model)
   int* d_n_i = nullptr;
   int* d_off = nullptr;      // unpadded column offsets (G+1)
   int* d_poff = nullptr;     // padded column offsets (G+1)

@@ -34,7 +34,7 @@ namespace glmsur {
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
 __global__ void __launch_bounds__(256)
-k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ g,
+k_sigma_step(int64_t M, int64_t Ms, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ g,
              T* __restrict__ u, T* __restrict__ w, T* __restrict__ S, T* __restrict__ wbest,
              PcgState st, const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -76,14 +76,17 @@ k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, 
       T uo[EB][V], gv[EB][V], wv[EB][V];
       int64_t gi[EB];
       int ee[EB];
+      bool live[EB];
 #pragma unroll
       for (int b = 0; b < EB; ++b) {
         const int e = e0 + b * blockDim.x;
         ee[b] = e;
+        live[b] = false;
         if (e < nu) {
           const int jv = e % (JJ / V), rest = e / (JJ / V);
           const int i = rest % G, t = rest / G;
           gi[b] = ((t0 + t) * G + i) * k + jg * JJ + jv * V;
+          live[b] = t0 + t < Ms;
 #pragma unroll
           for (int c = 0; c < V; ++c) {
             uo[b][c] = u[gi[b] + c];
@@ -108,7 +111,8 @@ k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, 
               un = gv[b][c] + (T)mu_s[jj] * un;
               u[gi[b] + c] = un;
             }
-            U_s[(int64_t)ee[b] * V + c] = un;
+            // rows t >= Ms have Sigma = 0 (restriction rows): S = U Omega sees zeros there
+            U_s[(int64_t)ee[b] * V + c] = live[b] ? un : (T)0;
           }
         }
       }
@@ -146,11 +150,12 @@ k_sigma_step(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, 
 }
 
 // ---------------------------------------------------------------------------
-// sigma_resid: E = Y - W Omega  (no state; used for b = X*^T (y - Sigma w))
+// sigma_resid: E = Y - W Omega on rows t < Ms, E = Y on the rows t >= Ms
+// (Sigma = 0 there); no state; used for b = X*^T (y - Sigma w)
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
 __global__ void __launch_bounds__(256)
-k_sigma_resid(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ Y,
+k_sigma_resid(int64_t M, int64_t Ms, int G, int Gq, int k, int TR, const T* __restrict__ Om, const T* __restrict__ Y,
               const T* __restrict__ Wv, T* E) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* Om_s = reinterpret_cast<T*>(smraw);
@@ -167,7 +172,7 @@ k_sigma_resid(int64_t M, int G, int Gq, int k, int TR, const T* __restrict__ Om,
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
       const int jj = e % JJ, rest = e / JJ;
       const int i = rest % G, t = rest / G;
-      U_s[e] = Wv[((t0 + t) * G + i) * k + jg * JJ + jj];
+      U_s[e] = t0 + t < Ms ? Wv[((t0 + t) * G + i) * k + jg * JJ + jj] : (T)0;
     }
     __syncthreads();
     const int nitems = tr * nhq * JJ;
@@ -938,7 +943,7 @@ constexpr bool kQuadSigma = sizeof(T) == 4 && JJ % 4 == 0 && JJ >= 4;
 
 template <typename T, int JJ, int RI>
 __global__ void __launch_bounds__(512, 1)
-k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict__ Om, const T* __restrict__ g,
+k_sigma_step_tma(int64_t M, int64_t Ms, int G, int Gq, int TR, int NST, const T* __restrict__ Om, const T* __restrict__ g,
                  T* __restrict__ u, T* __restrict__ w, T* __restrict__ S, T* __restrict__ wbest, PcgState st,
                  const double* __restrict__ cpart, int ncpart, double* __restrict__ dpart) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -1040,6 +1045,9 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
           reinterpret_cast<float4*>(u + row0 * GK)[e4] = uo;   // inactive lanes rewrite their u
           reinterpret_cast<float4*>(us)[e4] = uo;
         }
+        // rows t >= Ms have Sigma = 0 (restriction rows): the tile of U that
+        // S = U Omega reads is zero there (a float4 never straddles two rows)
+        if (row0 + (4 * e4) / GK >= Ms) reinterpret_cast<float4*>(us)[e4] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     } else {
       for (int e = tid; e < ne; e += blockDim.x) {
@@ -1054,6 +1062,7 @@ k_sigma_step_tma(int64_t M, int G, int Gq, int TR, int NST, const T* __restrict_
           u[row0 * GK + e] = un;
           us[e] = un;
         }
+        if (row0 + e / GK >= Ms) us[e] = (T)0;   // Sigma = 0 on rows t >= Ms
       }
     }
     __syncthreads();
@@ -1368,7 +1377,7 @@ static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const
                                  T* wbest, const PcgState& st, const double* cpart, double* dpart, cudaStream_t s) {
   if (p.tma_sigma) {
 #define SIG_(R)                                                                                                  \
-  k_sigma_step_tma<T, JJ, R><<<p.n_sigma, 512, p.sigma_tma_smem, s>>>(gm.M, gm.G, gm.Gq, p.tr_tma, p.nst_sigma, Om, \
+  k_sigma_step_tma<T, JJ, R><<<p.n_sigma, 512, p.sigma_tma_smem, s>>>(gm.M, gm.Ms, gm.G, gm.Gq, p.tr_tma, p.nst_sigma, Om, \
                                                                        g, u, w, S, wbest, st, cpart,          \
                                                                        p.n_cpart + p.extra_cpart, dpart)
     if (p.ri == 4) SIG_(4);
@@ -1379,7 +1388,7 @@ static void launch_sigma_step_jj(const IterPlan& p, const Geom& gm, int k, const
   }
   dim3 grid(p.n_sigma, 1, k / JJ);
   const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
-  k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, wbest, st, cpart,
+  k_sigma_step<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.Ms, gm.G, gm.Gq, k, p.TR, Om, g, u, w, S, wbest, st, cpart,
                                               p.n_cpart + p.extra_cpart, dpart);
 }
 
@@ -1388,7 +1397,7 @@ static void launch_sigma_resid_jj(const IterPlan& p, const Geom& gm, int k, cons
                                   T* E, cudaStream_t s) {
   dim3 grid(p.n_sigma, 1, k / JJ);
   const size_t smem = sizeof(T) * ((size_t)gm.G * gm.Gq + (size_t)p.TR * gm.G * JJ);
-  k_sigma_resid<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.G, gm.Gq, k, p.TR, Om, Y, W, E);
+  k_sigma_resid<T, JJ><<<grid, 256, smem, s>>>(gm.M, gm.Ms, gm.G, gm.Gq, k, p.TR, Om, Y, W, E);
 }
 
 template <typename T, int JJ>

@@ -182,6 +182,87 @@ class GlmSur:
             pass
 
 
+class GlmMvrglm:
+    """The restricted multivariate GLM Y = Z0 B + U (Sec. "Multivariate linear
+    models with parameters restrictions"), MVRGLM: model reduction by the QR
+    of Z0, the updating QRDs [R0; C_i] and PCG-Aug with the block-diagonal X*
+    and Pi.  Z0: (M, N); Omega0: (G, G); C_list: G matrices (k_i, N) (k_i = 0
+    allowed).  ``solve(Y, gamma=None)`` takes Y as (M, G) or (M, G, k) and
+    gamma as a list of G arrays (k_i,) or (k_i, k), and returns B as (N, G, k)."""
+
+    def __init__(self, Z0, Omega0, C_list, precision: str = "fp64", tol: float = 1e-13, maxit: int = 0,
+                 stagnation_window: int = 25, inner_tol: float = 1e-5, max_refine: int = 8, chunk: int = 16,
+                 precond: str = "identity", device="cuda"):
+        self.device = torch.device(device)
+        Z = _dev_f64(Z0, self.device)
+        self.M, self.N = Z.shape
+        Om = _dev_f64(Omega0, self.device)
+        self.G = Om.shape[0]
+        self.k_i = [int(torch.as_tensor(c).reshape(-1, self.N).shape[0]) for c in C_list]
+        self.ktot = sum(self.k_i)
+        Zcm = Z.t().contiguous()
+        Cs = [_dev_f64(c, self.device).reshape(-1, self.N) for c in C_list]
+        Ccm = torch.cat(Cs, dim=0).t().contiguous() if self.ktot > 0 else None
+        self.opts = L.default_opts()
+        self.opts.precision = PRECISIONS[precision]
+        self.opts.tol = tol
+        self.opts.maxit = maxit
+        self.opts.stagnation_window = stagnation_window
+        self.opts.inner_tol = inner_tol
+        self.opts.max_refine = max_refine
+        self.opts.chunk = chunk
+        self.opts.precond = PRECONDS[precond]
+        self._h = L.glm_sur_mvrglm_setup(self.G, self.M, self.N, Zcm.data_ptr(), self.M, Om.contiguous().data_ptr(),
+                                         self.k_i, Ccm.data_ptr() if Ccm is not None else 0, max(self.ktot, 1),
+                                         self.opts, GlmSur._stream())
+        torch.cuda.synchronize(self.device)
+        st = L.glm_sur_get_setup_status(self._h)
+        if st != L.GLM_SUR_OK:
+            self.close()
+            raise L.GlmSurError(st, "glm_sur_mvrglm_setup (updating QRDs)")
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def set_omega(self, Omega0) -> None:
+        O = _dev_f64(Omega0, self.device).contiguous()
+        L.glm_sur_set_omega(self._h, O.data_ptr(), GlmSur._stream())
+
+    def solve(self, Y, gamma=None) -> SolveResult:
+        Y = _dev_f64(Y, self.device)
+        if Y.dim() == 2:
+            Y = Y[:, :, None]
+        M, G, k = Y.shape
+        Ycm = Y.permute(2, 1, 0).contiguous()          # column j = vec(Y_j)
+        b = torch.empty((k, G * self.N), dtype=torch.float64, device=self.device)
+        iters = torch.zeros(k, dtype=torch.int32, device=self.device)
+        relres = torch.zeros(k, dtype=torch.float64, device=self.device)
+        if gamma is not None and self.ktot > 0:
+            gs = [_dev_f64(gi, self.device).reshape(ki, -1).expand(ki, k) for gi, ki in zip(gamma, self.k_i)
+                  if ki > 0]
+            gcm = torch.cat(gs, dim=0).t().contiguous()
+            L.glm_sur_solve_restricted(self._h, Ycm.data_ptr(), M * G, gcm.data_ptr(), self.ktot, k, b.data_ptr(),
+                                       G * self.N, iters.data_ptr(), relres.data_ptr(), GlmSur._stream())
+        else:
+            L.glm_sur_solve(self._h, Ycm.data_ptr(), M * G, k, b.data_ptr(), G * self.N, iters.data_ptr(),
+                            relres.data_ptr(), GlmSur._stream())
+        status = L.glm_sur_get_status(self._h, k)
+        B = b.view(k, G, self.N).permute(2, 1, 0)
+        return SolveResult(B, iters, relres, status)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            L.glm_sur_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class GlmSurBatch:
     """Many independent SUR instances solved in one persistent launch.
 

@@ -62,6 +62,10 @@ def test_host_only_calls(libpath):
     assert L.glm_sur_solve_restricted(None, 1, 1, None, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_set_restrictions(None, 1, 1, 1, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_solve_ne(None, 1, 1, 1, 1, 1, None, None, None) == _lib.GLM_SUR_INVALID_ARG
+    k_i = (ctypes.c_int * 2)(1, 70)    # more restrictions than regressors in equation 2
+    assert L.glm_sur_mvrglm_setup(ctypes.byref(h), 2, 100, 60, 1, 100, 1, k_i, 1, 71, None, None) == \
+        _lib.GLM_SUR_INVALID_ARG
+    assert L.glm_sur_mvrglm_setup(None, 2, 100, 60, 1, 100, 1, k_i, 1, 71, None, None) == _lib.GLM_SUR_INVALID_ARG
     bh = ctypes.c_void_p()
     g1 = (ctypes.c_int * 1)(2)
     m1 = (ctypes.c_int * 1)(100)

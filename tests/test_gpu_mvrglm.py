@@ -1,0 +1,142 @@
+"""MVRGLM on the GPU (glm_sur_mvrglm_setup): the restricted multivariate GLM
+of Sec. "Multivariate linear models with parameters restrictions" on the
+synthetic VAR(4) shapes of the paper's experiments (G = 12, M = 300, N = 60,
+sparsity 26 % / 80 %, largest root 0.90 / 1.05, cond(Omega0) 4.48 / 448),
+against the oracle's MVRGLM and against the SUR GLS estimate of the model
+with the excluded regressors removed (structured QR solver).  Tolerance:
+relative ||B - B_ref|| <= 1e-9 for the stationary series; the explosive
+series (cond(Z0) ~ 1e7) are held to 1e-6, the float64 sensitivity of the
+restricted estimate there."""
+import numpy as np
+import pytest
+
+from oracle import sur_oracle as O
+from synth import sur_inputs as S
+from synth import var_inputs as V
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_14471_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def scatter_free(p, b_free):
+    B = np.zeros((p.N, p.G, b_free.shape[1]))
+    off = 0
+    for i, f in enumerate(p.free):
+        B[f, i, :] = b_free[off:off + f.size]
+        off += f.size
+    return B
+
+
+def mv(p, **kw):
+    from paper_2510_14471_gb300.sur import GlmMvrglm
+    h = GlmMvrglm(p.Z0, p.Omega0, p.C_list, **kw)
+    r = h.solve(p.Y)
+    out = dict(B=r.b.cpu().numpy(), iters=r.iters.cpu().numpy(), status=r.status)
+    h.close()
+    return out
+
+
+VAR_CASES = [
+    # (sparsity, lam_max, omega_cond, tol_B)
+    (0.26, 0.90, 4.48, 1e-9),
+    (0.80, 0.90, 448.0, 1e-9),
+    (0.26, 1.05, 4.48, 1e-6),
+    (0.80, 1.05, 448.0, 1e-6),
+]
+
+
+@pytest.mark.parametrize("sparsity,lam,ocond,tol_b", VAR_CASES)
+def test_var_models_match_the_oracle(sparsity, lam, ocond, tol_b):
+    p = V.var_problem(sparsity=sparsity, lam_max=lam, omega_cond=ocond, k=4, seed=101)
+    r = mv(p, tol=1e-12, stagnation_window=200)
+    assert r["status"] == [0] * 4, (r["status"], r["iters"])
+    ref = scatter_free(p, O.sur_gls_structured(p.free_blocks(), p.Omega0, p.y_vec()))
+    assert rel(r["B"], ref) <= tol_b, rel(r["B"], ref)
+    orc = O.mvrglm_pcg_aug(p.Z0, p.Y, p.Omega0, p.C_list, p.gamma_list, tol=1e-12, stag_window=200,
+                           maxit=4 * sum(p.k_i) + 40)
+    assert rel(r["B"], orc["B"]) <= tol_b
+    # the excluded coefficients are zero
+    for i, f in enumerate(p.free):
+        mask = np.ones(p.N, dtype=bool)
+        mask[f] = False
+        assert np.max(np.abs(r["B"][mask, i, :])) <= 1e-10 * np.max(np.abs(r["B"]))
+
+
+def test_var_step_counts_follow_the_oracle():
+    p = V.var_problem(sparsity=0.26, lam_max=0.90, omega_cond=4.48, k=2, seed=103)
+    r = mv(p, tol=1e-10, stagnation_window=200)
+    orc = O.mvrglm_pcg_aug(p.Z0, p.Y, p.Omega0, p.C_list, p.gamma_list, tol=1e-10, stag_window=200,
+                           maxit=4 * sum(p.k_i) + 40)
+    it_g, it_o = r["iters"].astype(int), np.asarray(orc["iters"])
+    assert np.all(np.abs(it_g - it_o) <= np.maximum(3, 0.1 * it_o)), (it_g, it_o)
+
+
+def general_restrictions(seed, G=5, M=400, N=9, k_i=(3, 0, 5, 1, 9), k=3):
+    g = S.rng(seed)
+    Z0 = g.standard_normal((M, N))
+    A = g.standard_normal((G, G))
+    Om = A @ A.T / G + 0.5 * np.eye(G)
+    C_list = [g.standard_normal((ki, N)) for ki in k_i]
+    B = g.standard_normal((N, G))
+    gamma = [C_list[i] @ B[:, i:i + 1] * np.ones((1, k)) + 0.1 * g.standard_normal((k_i[i], k))
+             for i in range(G)]
+    U = np.einsum("mgk,hg->mhk", g.standard_normal((M, G, k)), np.linalg.cholesky(Om))
+    Y = np.einsum("mn,ng->mg", Z0, B)[:, :, None] + U
+    return Z0, Y, Om, C_list, gamma
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("precond", ["identity", "scaled", "diag"])
+def test_general_restrictions_with_gamma(precision, precond):
+    from paper_2510_14471_gb300.sur import GlmMvrglm
+    Z0, Y, Om, C_list, gamma = general_restrictions(107)
+    Om = np.diag([0.2, 1.0, 5.0, 1.0, 0.5]) @ Om @ np.diag([0.2, 1.0, 5.0, 1.0, 0.5])
+    h = GlmMvrglm(Z0, Om, C_list, precision=precision, precond=precond, tol=1e-12, stagnation_window=200)
+    r = h.solve(Y, gamma)
+    B = r.b.cpu().numpy()
+    assert all(s == 0 for s in r.status), r.status
+    orc = O.mvrglm_pcg_aug(Z0, Y, Om, C_list, gamma, tol=1e-12, stag_window=200)
+    assert rel(B, orc["B"]) <= 1e-9
+    for i in range(len(C_list)):
+        if C_list[i].shape[0]:
+            assert np.allclose(C_list[i] @ B[:, i, :], gamma[i], atol=1e-9 * np.abs(gamma[i]).max())
+    h.close()
+
+
+def test_no_restrictions_is_ols_without_steps():
+    from paper_2510_14471_gb300.sur import GlmMvrglm
+    Z0, Y, Om, _, _ = general_restrictions(109)
+    G, N = Om.shape[0], Z0.shape[1]
+    h = GlmMvrglm(Z0, Om, [np.zeros((0, N))] * G)
+    r = h.solve(Y)
+    B_ols = np.stack([np.linalg.lstsq(Z0, Y[:, :, j], rcond=None)[0] for j in range(Y.shape[2])], axis=2)
+    assert list(r.iters.cpu().numpy()) == [0, 0, 0]
+    assert rel(r.b.cpu().numpy(), B_ols) <= 1e-12
+    h.close()
+
+
+def test_mvrglm_refusals():
+    from paper_2510_14471_gb300 import _lib as L
+    from paper_2510_14471_gb300.sur import GlmMvrglm
+    Z0, Y, Om, C_list, gamma = general_restrictions(113)
+    h = GlmMvrglm(Z0, Om, C_list)
+    h.solve(Y, gamma)
+    handle = h.handle
+    assert L.lib().glm_sur_backward(handle, 1, 1, 1, 1, 1, None, 1, None, None, None) == L.GLM_SUR_INVALID_ARG
+    assert L.lib().glm_sur_solve_ne(handle, 1, 10 ** 6, 1, 1, 10 ** 6, None, None, None) == L.GLM_SUR_INVALID_ARG
+    assert L.lib().glm_sur_set_restrictions(handle, 1, 1, 1, None) == L.GLM_SUR_INVALID_ARG
+    h.close()
+    # rank-deficient Z0
+    Zb = Z0.copy()
+    Zb[:, 3] = Zb[:, 1]
+    with pytest.raises(L.GlmSurError):
+        GlmMvrglm(Zb, Om, C_list)
