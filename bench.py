@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--profile-reps", type=int, default=20)
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the batched, constrained and differentiable summaries")
-    ap.add_argument("--workload", default="singular", choices=["singular", "batched", "constrained", "differentiable"],
+    ap.add_argument("--workload", default="singular",
+                    choices=["singular", "batched", "constrained", "differentiable", "var"],
                     help="singular: the headline workload; the others measure the batched, restricted and "
                          "adjoint paths on their own workloads")
     return ap.parse_args()
@@ -186,7 +187,7 @@ def ncu_traffic(args, kernel):
     return None
 
 
-EXTRA_WORKLOADS = ("batched", "constrained", "differentiable")
+EXTRA_WORKLOADS = ("batched", "constrained", "differentiable", "var")
 
 
 def run_extras(timeout_s=420):
@@ -212,7 +213,7 @@ def run_extras(timeout_s=420):
             continue
         keep = ["value", "unit", "ms_per_step", "dtype", "config", "roofline", "roofline_iter", "e2e", "gpu_launches",
                 "clocks", "rel_err_sampled", "rel_err", "status_counts", "steps_per_instance", "iters_max", "k1",
-                "grad_err", "b_err", "steps"]
+                "grad_err", "b_err", "steps", "models"]
         out[w] = {k2: line[k2] for k2 in keep if k2 in line}
         out[w]["wall_s"] = time.perf_counter() - t0
     return out
@@ -860,6 +861,93 @@ def run_differentiable(args, rank, world, local, pg):
     return 0
 
 
+# the six restricted VAR models of the paper's second experiment (sparsity
+# factor, largest root, condition number of Omega0), on synthetic data
+VAR_MODELS = ((0.26, 0.90, 4.48), (0.26, 1.05, 4.48), (0.26, 0.90, 448.0), (0.26, 1.05, 448.0),
+              (0.80, 0.90, 448.0), (0.80, 1.05, 448.0))
+
+
+def run_var(args, rank, world, local, pg):
+    """Restricted VAR(4) models, G = 12, M = 300, N = 60, k = 1: MVRGLM and
+    PCG-Aug (the SUR model without the excluded regressors) with D = alpha I
+    (K1) and D = diag(Sigma) (K2), and PCG-NE, each to tol 1e-12; steps, time
+    per solve and the error against the oracle's structured GLS solve."""
+    import torch
+    from paper_2510_14471_gb300 import build
+    if rank == 0:
+        build.build()
+    if pg is not None:
+        pg.barrier()
+    from paper_2510_14471_gb300 import _lib as L
+    from paper_2510_14471_gb300.sur import GlmMvrglm, GlmSur
+    from synth import var_inputs as V
+    from oracle import sur_oracle as O
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    models = []
+    launches = 0
+    total_ms = 0.0
+    total_solves = 0
+    clocks_all = None
+    for mi, (sp, lam, oc) in enumerate(VAR_MODELS):
+        p = V.var_problem(sparsity=sp, lam_max=lam, omega_cond=oc, k=1, seed=2510014471 + 50 + mi)
+        ref_free = O.sur_gls_structured(p.free_blocks(), p.Omega0, p.y_vec())
+        ref = np.zeros((p.N, p.G))
+        off = 0
+        for i, f in enumerate(p.free):
+            ref[f, i] = ref_free[off:off + f.size, 0]
+            off += f.size
+        row = {"sparsity": sp, "lam_max": lam, "omega_cond": oc, "restrictions": int(sum(p.k_i)),
+               "cond_Z0": float(np.linalg.cond(p.Z0))}
+        Yd = torch.as_tensor(p.Y, device=dev)
+        yv = torch.as_tensor(p.y_vec(), device=dev)
+        for name, make, call, to_b in (
+                ("mvrglm_K1", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="scaled", tol=1e-12,
+                                                stagnation_window=200, device=dev),
+                 lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
+                ("mvrglm_K2", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="diag", tol=1e-12,
+                                                stagnation_window=200, device=dev),
+                 lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
+                ("pcg_aug_K1", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="scaled", tol=1e-12,
+                                              stagnation_window=200, device=dev),
+                 lambda h: h.solve(yv), None),
+                ("pcg_aug_K2", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="diag", tol=1e-12,
+                                              stagnation_window=200, device=dev),
+                 lambda h: h.solve(yv), None),
+                ("pcg_ne", lambda: GlmSur(p.free_blocks(), p.Omega0, tol=1e-12, maxit=20000, device=dev),
+                 lambda h: h.solve_ne(yv), None)):
+            h = make()
+            r = call(h)
+            torch.cuda.synchronize()
+            l0 = L.glm_sur_launch_count(h.handle)
+            ms, clocks = timed(lambda: call(h), args.steps, args.warmup, local, pg)
+            launches += (L.glm_sur_launch_count(h.handle) - l0) * args.steps // (args.steps + args.warmup)
+            clocks_all = clocks if clocks_all is None else clocks_all
+            if to_b is not None:
+                B = to_b(r)
+            else:
+                bf = r.b[:, 0].cpu().numpy()
+                B = np.zeros((p.N, p.G))
+                off = 0
+                for i, f in enumerate(p.free):
+                    B[f, i] = bf[off:off + f.size]
+                    off += f.size
+            row[name] = {"steps": int(r.iters.max().item()), "ms": float(ms), "status": [int(v) for v in r.status],
+                         "rel_err": float(np.linalg.norm(B - ref) / np.linalg.norm(ref))}
+            total_ms += float(ms)
+            total_solves += 1
+            h.close()
+        models.append(row)
+    if rank == 0:
+        line = base_line(args, world, "restricted VAR solves/s (MVRGLM, PCG-Aug, PCG-NE)",
+                         "var-g12-m300-n60 (six restricted VAR(4) models, k=1)",
+                         1000.0 * total_solves / total_ms, "solves/s", total_ms / total_solves, "f64",
+                         {"workload": "var-g12-m300-n60", "G": 12, "M": 300, "N": 60, "k": 1})
+        line.update({"models": models, "gpu_launches": int(launches), "clocks": clocks_all})
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_init(args)
@@ -872,6 +960,8 @@ def main():
             return run_constrained(args, rank, world, local, pg)
         if args.workload == "differentiable":
             return run_differentiable(args, rank, world, local, pg)
+        if args.workload == "var":
+            return run_var(args, rank, world, local, pg)
         return run_ours(args, rank, world, local, pg)
     finally:
         if pg is not None:
