@@ -8,7 +8,7 @@
  *                                      Sigma = Omega (x) I_M,  Omega G x G, PSD.
  *   GLS as the augmented system eq. (aug1):  [Sigma X; X^T 0][w; b] = [y; 0].
  *   Solved by Algorithm glmpcg2 (PCG-Aug) with the indefinite preconditioner
- *   eq. (invprec) and D = I (Sec. 5.3): every step applies Sigma as U * Omega
+ *   eq. (invprec) and D = I (Sec. 4.3): every step applies Sigma as U * Omega
  *   and the per-block OLS projection Pi_i = I - Q_i Q_i^T from a Householder
  *   QR X_i = Q_i R_i computed once; the estimate is z = X*^T (y - Sigma w)
  *   with X*^T xi = vec(R_i^-1 Q_i^T xi_i).
@@ -75,14 +75,17 @@ typedef struct {
   int reduce_rows;        /* setup only: 1 = solve the row-reduced model of Remark
                              rem:reduction (M' = n rows), when M >= 2 n,
                              n <= 2048 and W = [X_1 ... X_G] has full column
-                             rank (otherwise the model is kept whole)         */
+                             rank (otherwise the model is kept whole).  On a
+                             reduced handle tol, relres and the stop tests
+                             refer to the reduced system (responses Q^T y_i),
+                             not to the M-row model                          */
   int step_kernels;       /* GLM_SUR_STEP_*: kernels of the float32 bulk steps   */
   int precond;            /* GLM_SUR_PRECOND_*: the block D of the preconditioner
                              of eq. (invprec), D = D0 (x) I_M               */
 } glm_sur_opts;
 
 enum {
-  GLM_SUR_PRECOND_IDENTITY = 0,  /* D = I (Sec. 5.3)                             */
+  GLM_SUR_PRECOND_IDENTITY = 0,  /* D = I (Sec. 4.3)                             */
   GLM_SUR_PRECOND_SCALED = 1,    /* D = alpha I, alpha = max_i omega_ii          */
   GLM_SUR_PRECOND_DIAG = 2       /* D = diag(Sigma) = diag(Omega) (x) I_M (the two
                                     choices of the VAR experiments).  With D0 =
@@ -114,7 +117,7 @@ void glm_sur_default_opts(glm_sur_opts* opts);
 
 /*
  * glm_sur_setup -- factor the regressors once (Sec. 3.2: the factorisations
- * the preconditioner needs do not change between steps; Sec. 5.3: X_i = Q_i R_i).
+ * the preconditioner needs do not change between steps; Sec. 4.3: X_i = Q_i R_i).
  *
  *   out    : receives the new handle (host pointer).
  *   G      : number of equations, 1 <= G <= 1024.  Solves need G <= 156:
@@ -139,7 +142,7 @@ glm_sur_status glm_sur_setup(glm_sur_t* out, int G, int64_t M, const int* n_i,
  * GLM_SUR_RANK_DEFICIENT (a block with |R_jj| <= n_i * eps * max|R|). */
 glm_sur_status glm_sur_get_setup_status(glm_sur_t h);
 
-/* Replace Omega (DEVICE, G x G) without refactoring X (Sec. 5.3: the QRs
+/* Replace Omega (DEVICE, G x G) without refactoring X (Sec. 4.3: the QRs
  * depend on X only). */
 glm_sur_status glm_sur_set_omega(glm_sur_t h, const double* Omega, glm_sur_stream_t stream);
 
@@ -168,7 +171,7 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k,
 
 /*
  * glm_sur_set_restrictions -- linear restrictions C b = d on the parameters
- * (Sec. 5.1): the model becomes the GLM of eq. (RGLM1setup) with
+ * (Sec. 4.1): the model becomes the GLM of eq. (RGLM1setup) with
  * Sigma_aug = diag(Omega (x) I_M, 0), X_aug = [(+)X_i; C], y_aug = [y; d],
  * and the preconditioner of eq. (invprec) with D = I, whose X* and Pi are
  * those of eq. (rglm1m): N = X_aug^T X_aug = (+)R_i^T R_i + C^T C is formed
@@ -185,7 +188,7 @@ glm_sur_status glm_sur_set_restrictions(glm_sur_t h, const double* C, int64_t ld
 /*
  * glm_sur_solve_restricted -- glm_sur_solve for a handle with restrictions:
  * Algorithm glmpcg2 on the restricted GLM (at most m + kc - n + 1 steps in
- * exact arithmetic, Sec. 5.1), b = X*^T (y_aug - Sigma_aug w).
+ * exact arithmetic, Sec. 4.1), b = X*^T (y_aug - Sigma_aug w).
  *   d  : DEVICE, kc x k column-major, ldd >= kc; NULL means d = 0.
  * Other arguments as glm_sur_solve.  (glm_sur_solve on a restricted handle
  * solves with d = 0.)

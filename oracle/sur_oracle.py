@@ -16,10 +16,10 @@ of General Linear Models"):
   * ``ols_blocks``        -- per-block OLS of the SUR model (Sec. 1).
   * ``sur_gls_structured``-- structured direct GLS: Remark rem:reduction, then
                              an eigen-split of Omega; zero-variance directions
-                             become exact restrictions (Sec. 5.1 idea).
+                             become exact restrictions (Sec. 4.1 idea).
   * ``pcg``               -- Algorithm pcg on dense (G, K, h).
   * ``sur_pcg_aug``       -- Algorithm glmpcg2 (PCG-Aug) in the SUR form of
-                             Sec. 5.3 (per-block QR, Sigma u = vec(U Omega)),
+                             Sec. 4.3 (per-block QR, Sigma u = vec(U Omega)),
                              D = I or D = diag(delta) (x) I_M (alpha I, diag(Sigma));
                              also carries the z-iterates of Algorithm glmpcg.
   * ``sur_pcg_aug3``      -- Algorithm glmpcg3 (s-recurrence), fixed steps.
@@ -31,7 +31,7 @@ of General Linear Models"):
                              QRDs [R0; C_i] = Qt_i R_i, Algorithm glmpcg2 with
                              the block-diagonal X* and Pi.
   * ``rglm_pcg_aug``      -- the same algorithm on the restricted GLM of
-                             Sec. 5.1 (eq. RGLM1setup, eq. rglm1m with D = I).
+                             Sec. 4.1 (eq. RGLM1setup, eq. rglm1m with D = I).
   * ``sur_gls_gradient``  -- adjoint of eq. (aug1) for L(b): dL/dy and dL/dOmega.
   * ``sur_gls_gradient_kron`` -- the same adjoint for positive definite Omega
     through Sigma^-1 = Omega^-1 (x) I_M (medium sizes, no m x m matrix).
@@ -279,7 +279,7 @@ def pcg(Gm, Km, h, x1, iters):
 
 
 class SurOps:
-    """The SUR applies of Sec. 5.3 from thin QRs X_i = Q_i R_i, with the
+    """The SUR applies of Sec. 4.3 from thin QRs X_i = Q_i R_i, with the
     preconditioner block D = D_0 (x) I_M, D_0 = diag(delta) (D = I when delta
     is not given).  From eq. (Xstar): X* = D^-1 X (X^T D^-1 X)^-1 and
     Pi = (I - X* X^T) D^-1; with block i of D equal to delta_i I the delta_i
@@ -350,7 +350,7 @@ STATUS_NOT_CONVERGED = "not_converged"
 
 def sur_pcg_aug(X_blocks, Omega, Y, tol=1e-13, maxit=None, stag_window=25,
                 record=False, ops=None, w1=None, delta=None):
-    """Algorithm glmpcg2 (PCG-Aug) in the SUR form of Sec. 5.3 (O3), with the
+    """Algorithm glmpcg2 (PCG-Aug) in the SUR form of Sec. 4.3 (O3), with the
     preconditioner block D = diag(delta) (x) I_M (D = I by default; Sec. 3.3
     and the VAR experiments use D = alpha I and D = diag(Sigma)).
 
@@ -637,7 +637,7 @@ def scaled_identity_delta(Omega):
 
 
 def rglm_pcg_aug(X_blocks, Omega, Y, C, d, tol=1e-13, maxit=None, stag_window=25):
-    """Algorithm glmpcg2 on the restricted GLM of Sec. 5.1 with D = I.
+    """Algorithm glmpcg2 on the restricted GLM of Sec. 4.1 with D = I.
 
     eq. (RGLM1setup): Sigma_aug = diag(Omega (x) I_M, 0_kc), X_aug = [(+)X_i; C],
     y_aug = [y; d].  eq. (rglm1m) with D_Z = I, D_C = I:

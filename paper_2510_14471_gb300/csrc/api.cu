@@ -103,7 +103,7 @@ struct glm_sur_ctx {
   int plan_k = -1, plan_prec = -1;
   bool has_w = false;
   int64_t launches = 0;        // kernel launches issued (graph nodes included)
-  // linear restrictions C b = d (Sec. 5.1)
+  // linear restrictions C b = d (Sec. 4.1)
   int kc = 0;
   double* Cmat = nullptr;      // kc x n column-major (ld = kc)
   double* Nmat = nullptr;      // n x n: X_aug^T X_aug, then its Cholesky factor
@@ -475,7 +475,7 @@ void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
     launch_reduce<T>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
     const T* Cupd = C;
     if (h->kc > 0 && sizeof(T) == sizeof(double)) {
-      // restricted GLM (Sec. 5.1): c = N^-1 [R_i^T e_i], f_i = R_i c_i, g_C += lambda C c
+      // restricted GLM (Sec. 4.1): c = N^-1 [R_i^T e_i], f_i = R_i c_i, g_C += lambda C c
       rglm_coef(h->gm, k, reinterpret_cast<const double*>(C), h->R, h->Minv, h->Cmat, h->kc, h->kc, nullptr, 0, 0.0,
                 h->cbuf, h->fbuf, nullptr, 0, s);
       rglm_gc(h->gm, k, h->kc, h->Cmat, h->kc, h->cbuf, nullptr, 0, h->st.lam, 0, h->gC, h->cpart, p.n_cpart, s);
@@ -528,7 +528,7 @@ glm_sur_status run_steps(glm_sur_ctx* h, int k, int maxit, cudaStream_t s) {
 }
 
 // g = -P y  (first residual of the PCG started at w = 0), u = w = 0, partials of g^T g.
-// Restricted (d != null or kc > 0): g = -Pi y_aug, y_aug = [y; d] (Sec. 5.1).
+// Restricted (d != null or kc > 0): g = -Pi y_aug, y_aug = [y; d] (Sec. 4.1).
 template <typename T>
 glm_sur_status pcg_init(glm_sur_ctx* h, int k, const T* y_layout, cudaStream_t s, const double* d = nullptr,
                         int64_t ldd = 0) {
@@ -585,7 +585,7 @@ glm_sur_status project_correction(glm_sur_ctx* h, int k, const IterPlan& p64, cu
   return GLM_SUR_OK;
 }
 
-// b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 5.3);
+// b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 4.3);
 // restricted: b = N^-1 ([R_i^T Q_i^T (y - Sigma w)_i] + C^T d)  (eq. rglm1m)
 glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, int64_t ldb, cudaStream_t s,
                          const double* d = nullptr, int64_t ldd = 0) {

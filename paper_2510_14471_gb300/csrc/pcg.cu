@@ -1,5 +1,5 @@
 // PCG-Aug iteration kernels for the SUR model (Algorithm glmpcg2 with D = I,
-// Sec. 5.3).  With D = I the preconditioner block Pi = (+)_i (I - Q_i Q_i^T)
+// Sec. 4.3).  With D = I the preconditioner block Pi = (+)_i (I - Q_i Q_i^T)
 // =: P is an orthogonal projector, so the iteration keeps g = P r
 // (c = r^T Pi r = g^T g) and, because P X v = 0, updates it by
 // g <- g - lambda P (Sigma u): the X v term of step 7 never has to be formed.
@@ -8,10 +8,10 @@
 //   sigma_step     : c_i from the partial sums of the previous step, the stop
 //                    tests and mu_{i-1} = c_i / c_{i-1} (every CTA computes the
 //                    same values); the lagged w_i = w_{i-1} - lambda_{i-1} u_{i-1};
-//                    u_i = g_i + mu_{i-1} u_{i-1}; S = U Omega (Sigma u, Sec. 5.3);
+//                    u_i = g_i + mu_{i-1} u_{i-1}; S = U Omega (Sigma u, Sec. 4.3);
 //                    partial sums of d_i = u_i^T S (step 5).
 //   proj_partial   : partial sums over row ranges of C_i = Q_i^T S_i (X*^T-like
-//                    apply of Sec. 5.3 without the R^-1).
+//                    apply of Sec. 4.3 without the R^-1).
 //   reduce         : C = sum of partials (fixed order); lambda_i = c_i / d_i
 //                    (step 6) and the breakdown test d_i <= 0.
 //   proj_update    : t = S - Q C (= P Sigma u), g_{i+1} = g_i - lambda_i t

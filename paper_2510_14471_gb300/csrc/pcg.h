@@ -19,7 +19,7 @@ struct IterPlan {
   int n_update = 1;        // row CTAs of proj_update
   int n_ugroups = 1;       // block groups of proj_update
   int n_cpart = 1;         // c partials written per step (n_update * n_ugroups)
-  int extra_cpart = 0;     // + 1 partial for the restriction rows (Sec. 5.1)
+  int extra_cpart = 0;     // + 1 partial for the restriction rows (Sec. 4.1)
   int ug_threads = 32;     // threads of a proj_update CTA (>= quads of any group)
   int ug_max_quads = 1;    // quads of the largest block group
   int TRB = 1;             // rows per proj_update tile

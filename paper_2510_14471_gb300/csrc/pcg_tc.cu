@@ -1,9 +1,9 @@
 // Fused float32 PCG-Aug step with the Sigma-apply on the fifth-generation
-// tensor cores (Algorithm glmpcg2 with D = I, Sec. 5.3).
+// tensor cores (Algorithm glmpcg2 with D = I, Sec. 4.3).
 //
 // One step is three launches:
 //   pass A : prologue (c_i, stop tests, mu_{i-1}); u_i = g_i + mu_{i-1} u_{i-1};
-//            S = U Omega (Sigma u, Sec. 5.3) on the tensor cores; partial sums
+//            S = U Omega (Sigma u, Sec. 4.3) on the tensor cores; partial sums
 //            of d_i = u_i^T S (step 5) and of C = Q_i^T S_i per block (the
 //            projection's X*^T-like apply without R^-1).
 //   reduce : C = sum of the partials, lambda_i = c_i / d_i (k_reduce).

@@ -1,5 +1,5 @@
 // Batched tall-skinny Householder QR of the regressor blocks X_i (setup, once
-// per handle).  Sec. 5.3: X_i = Q_i R_i with Q_i (M x n_i) orthonormal columns
+// per handle).  Sec. 4.3: X_i = Q_i R_i with Q_i (M x n_i) orthonormal columns
 // and R_i upper triangular; Sec. 3.2: the factorisations of the auxiliary OLS
 // problem are computed once and only applied in the iterations.
 //

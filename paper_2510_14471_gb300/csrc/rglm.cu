@@ -1,4 +1,4 @@
-// Linear restrictions C b = d folded into the augmented system (Sec. 5.1):
+// Linear restrictions C b = d folded into the augmented system (Sec. 4.1):
 // eq. (RGLM1setup) Sigma_aug = diag(Omega (x) I_M, 0), X_aug = [(+)X_i; C],
 // y_aug = [y; d], preconditioner eq. (invprec) with D = I.  With X_i = Q_i R_i,
 // X_aug^T X_aug = (+) R_i^T R_i + C^T C =: N, and (eq. rglm1m with D = I)

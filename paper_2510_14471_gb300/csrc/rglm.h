@@ -1,4 +1,4 @@
-// Linear restrictions folded into the augmented system (Sec. 5.1).
+// Linear restrictions folded into the augmented system (Sec. 4.1).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

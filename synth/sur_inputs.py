@@ -9,7 +9,7 @@ Every problem is drawn from numpy's counter-based Philox4x32-10 generator
 (Salmon et al., SC'11), keyed by ``seed`` so that a (seed, shape) pair always
 yields the same bytes on every machine.
 
-Model (SUR, paper Sec. 1 and Sec. 5.3, eq. SURdefs):
+Model (SUR, paper Sec. 1 and Sec. 4.3, eq. SURdefs):
     y = vec(Y),  X = (+)_i X_i,  Sigma = Omega (x) I_M,
     y = X beta + eps,  eps = (F (x) I_M) z,  z iid N(0, 1),  Omega = F F^T.
 With vec stacking columns, (F (x) I_M) vec(Z) = vec(Z F^T) for Z of shape

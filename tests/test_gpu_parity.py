@@ -3,7 +3,7 @@
 Tolerance: the target accuracy of the method is a relative error
 ||b - b_oracle|| / ||b_oracle|| <= 1e-9 per right-hand side (float64 PCG and
 float32-bulk + float64 refinement alike); QR factors are checked at the
-float64 rounding level of a Householder QR (Sec. 5.3 factorisation)."""
+float64 rounding level of a Householder QR (Sec. 4.3 factorisation)."""
 import numpy as np
 import pytest
 
@@ -183,7 +183,7 @@ def test_full_size_singular_workload_recovers_beta_true(precision, k):
     assert relcols(r["b"], p.beta) <= TOL_B, (r["status"], r["iters"])
 
 
-# ------------------------------------------------------------------ linear restrictions (Sec. 5.1)
+# ------------------------------------------------------------------ linear restrictions (Sec. 4.1)
 
 def gpu_solve_restricted(p, **kw):
     h = _glmsur()(p.X_blocks, p.Omega, precision="fp64", **kw)
@@ -213,7 +213,7 @@ def test_restricted_iterations_match_reference_pcg():
     r = gpu_solve_restricted(p, tol=1e-10)
     assert np.all(np.abs(r["iters"].astype(int) - ref["iters"].astype(int)) <= 2), (r["iters"], ref["iters"])
     assert relcols(r["b"], ref["b"]) <= TOL_B
-    # at most m + kc - n + 1 steps (Sec. 5.1)
+    # at most m + kc - n + 1 steps (Sec. 4.1)
     assert max(r["iters"]) <= p.m + 4 - p.n + 1
 
 

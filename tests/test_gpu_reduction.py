@@ -48,8 +48,15 @@ def test_reduced_estimate_matches_oracle(precision, omega, rank):
 def test_reduction_falls_back_when_w_is_rank_deficient():
     # equal regressors in every equation: W has rank n_1 < n, the model is kept whole
     p = S.make_problem(G=3, M=800, n_i=[4, 4, 4], k=2, seed=602, omega="chol", equal_X=True)
-    r = solver(p, reduce_rows=True).solve(p.Y)
+    h = solver(p, reduce_rows=True)
+    r = h.solve(p.Y)
     assert relcols(r.b.cpu().numpy(), O.sur_gls_structured(p.X_blocks, p.Omega, p.Y)) <= TOL
+    # the handle is the unreduced one: its factors are available (a reduced
+    # handle refuses glm_sur_get_factors) and Q has the model's M rows
+    Q, Rs = h.factors()
+    assert Q.shape == (800, 12)
+    Qn = Q.cpu().numpy()
+    assert np.allclose(Qn[:, :4] @ Rs[0].cpu().numpy(), p.X_blocks[0], atol=1e-10)
 
 
 def test_reduced_restricted_estimate():

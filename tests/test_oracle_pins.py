@@ -70,7 +70,7 @@ def test_diagonal_omega_gives_blockwise_ols():
 
 
 def test_equal_regressors_give_ols():
-    # all X_i equal (multivariate model, Sec. 1 / Sec. 5.2): GLS = OLS
+    # all X_i equal (multivariate model, Sec. 1 / Sec. 4.2): GLS = OLS
     p = S.make_problem(G=4, M=30, n_i=[3], k=1, seed=4, omega="chol", equal_X=True)
     b_ols = O.ols_blocks(p.X_blocks, p.Y)
     _, b1 = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
@@ -151,7 +151,7 @@ def _dense_pcg_w_iterates(p, iters):
 
 
 def test_glmpcg2_matches_generic_pcg_iterates():
-    # Algorithm glmpcg2 in the SUR form of Sec. 5.3 must reproduce the
+    # Algorithm glmpcg2 in the SUR form of Sec. 4.3 must reproduce the
     # w-iterates of Algorithm pcg on (G, K) built densely (eq. Gaug, invprec).
     p = S.make_problem(G=3, M=12, n_i=[2, 3, 2], k=1, seed=7, omega="chol")
     res = O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=0.0, maxit=6, stag_window=100,
@@ -238,7 +238,7 @@ def test_pcg_matches_dense_on_config0():
     assert res["status"][0] == O.STATUS_CONVERGED
 
 
-# ---------------------------------------------------------------- restrictions (Sec. 5.1)
+# ---------------------------------------------------------------- restrictions (Sec. 4.1)
 
 def test_restricted_models_agree_and_satisfy_constraints():
     p = S.make_problem(G=3, M=14, n_i=[3, 3, 2], k=2, seed=31, omega="spectrum", n_constraints=3)
@@ -249,7 +249,7 @@ def test_restricted_models_agree_and_satisfy_constraints():
     assert rel(res["b"], b1) < 1e-9
     for b in (b1, b2, res["b"]):
         assert np.linalg.norm(p.C @ b - p.d) < 1e-10 * np.linalg.norm(p.d)
-    # at most m + k - n + 1 steps (Sec. 5.1)
+    # at most m + k - n + 1 steps (Sec. 4.1)
     assert max(res["iters"]) <= p.m + 3 - p.n + 1
 
 
