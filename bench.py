@@ -870,7 +870,8 @@ VAR_MODELS = ((0.26, 0.90, 4.48), (0.26, 1.05, 4.48), (0.26, 0.90, 448.0), (0.26
 def run_var(args, rank, world, local, pg):
     """Restricted VAR(4) models, G = 12, M = 300, N = 60, k = 1: MVRGLM and
     PCG-Aug (the SUR model without the excluded regressors) with D = alpha I
-    (K1) and D = diag(Sigma) (K2), and PCG-NE, each to tol 1e-12; steps, time
+    (K1) and D = diag(Sigma) (K2), and PCG-NE, each to tol 1e-10 (the
+    explosive models floor near 1e-9 .. 1e-8 and end stagnated); steps, time
     per solve and the error against the oracle's structured GLS solve."""
     import torch
     from paper_2510_14471_gb300 import build
@@ -902,19 +903,19 @@ def run_var(args, rank, world, local, pg):
         Yd = torch.as_tensor(p.Y, device=dev)
         yv = torch.as_tensor(p.y_vec(), device=dev)
         for name, make, call, to_b in (
-                ("mvrglm_K1", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="scaled", tol=1e-12,
-                                                stagnation_window=200, device=dev),
+                ("mvrglm_K1", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="scaled", tol=1e-10,
+                                                stagnation_window=200, maxit=5000, device=dev),
                  lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
-                ("mvrglm_K2", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="diag", tol=1e-12,
-                                                stagnation_window=200, device=dev),
+                ("mvrglm_K2", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="diag", tol=1e-10,
+                                                stagnation_window=200, maxit=5000, device=dev),
                  lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
-                ("pcg_aug_K1", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="scaled", tol=1e-12,
-                                              stagnation_window=200, device=dev),
+                ("pcg_aug_K1", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="scaled", tol=1e-10,
+                                              stagnation_window=200, maxit=5000, device=dev),
                  lambda h: h.solve(yv), None),
-                ("pcg_aug_K2", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="diag", tol=1e-12,
-                                              stagnation_window=200, device=dev),
+                ("pcg_aug_K2", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="diag", tol=1e-10,
+                                              stagnation_window=200, maxit=5000, device=dev),
                  lambda h: h.solve(yv), None),
-                ("pcg_ne", lambda: GlmSur(p.free_blocks(), p.Omega0, tol=1e-12, maxit=20000, device=dev),
+                ("pcg_ne", lambda: GlmSur(p.free_blocks(), p.Omega0, tol=1e-10, maxit=20000, device=dev),
                  lambda h: h.solve_ne(yv), None)):
             h = make()
             r = call(h)

@@ -1436,7 +1436,8 @@ glm_sur_status glm_sur_solve(glm_sur_t h, const double* Y, int64_t ldy, int k, d
 glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd,
                                         int k, double* b, int64_t ldb, int* iters, double* relres,
                                         glm_sur_stream_t stream) {
-  if (!h || (h->sub ? h->sub->kc : h->kc) == 0) return GLM_SUR_INVALID_ARG;
+  if (!h) return GLM_SUR_INVALID_ARG;
+  if (h->mv_N == 0 && (h->sub ? h->sub->kc : h->kc) == 0) return GLM_SUR_INVALID_ARG;   // no restrictions
   return solve_impl(h, Y, ldy, d, ldd, k, b, ldb, iters, relres, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -46,23 +46,27 @@ def mv(p, **kw):
 
 
 VAR_CASES = [
-    # (sparsity, lam_max, omega_cond, tol_B)
-    (0.26, 0.90, 4.48, 1e-9),
-    (0.80, 0.90, 448.0, 1e-9),
-    (0.26, 1.05, 4.48, 1e-6),
-    (0.80, 1.05, 448.0, 1e-6),
+    # (sparsity, lam_max, omega_cond, solve tol, tol_B, allowed statuses).  The
+    # oracle's MVRGLM on these inputs: 62 steps; about 2400 steps (cond(Omega0)
+    # = 448 with 576 restrictions, far beyond the sum k_i + 1 of exact
+    # arithmetic); and for the explosive series (cond(Z0) ~ 1e7) a residual
+    # floor of 8e-10 and 2e-8 with estimate errors 5.6e-10 and 1.5e-7, where a
+    # column may end stagnated (status 4) at its floor.
+    (0.26, 0.90, 4.48, 1e-12, 1e-9, (0,)),
+    (0.80, 0.90, 448.0, 1e-12, 1e-9, (0,)),
+    (0.26, 1.05, 4.48, 1e-9, 1e-6, (0, 4)),
+    (0.80, 1.05, 448.0, 1e-9, 1e-6, (0, 4)),
 ]
 
 
-@pytest.mark.parametrize("sparsity,lam,ocond,tol_b", VAR_CASES)
-def test_var_models_match_the_oracle(sparsity, lam, ocond, tol_b):
+@pytest.mark.parametrize("sparsity,lam,ocond,tol,tol_b,ok", VAR_CASES)
+def test_var_models_match_the_oracle(sparsity, lam, ocond, tol, tol_b, ok):
     p = V.var_problem(sparsity=sparsity, lam_max=lam, omega_cond=ocond, k=4, seed=101)
-    r = mv(p, tol=1e-12, stagnation_window=200)
-    assert r["status"] == [0] * 4, (r["status"], r["iters"])
+    r = mv(p, tol=tol, stagnation_window=200, maxit=5000)
+    assert all(s in ok for s in r["status"]), (r["status"], r["iters"])
     ref = scatter_free(p, O.sur_gls_structured(p.free_blocks(), p.Omega0, p.y_vec()))
     assert rel(r["B"], ref) <= tol_b, rel(r["B"], ref)
-    orc = O.mvrglm_pcg_aug(p.Z0, p.Y, p.Omega0, p.C_list, p.gamma_list, tol=1e-12, stag_window=200,
-                           maxit=4 * sum(p.k_i) + 40)
+    orc = O.mvrglm_pcg_aug(p.Z0, p.Y, p.Omega0, p.C_list, p.gamma_list, tol=tol, stag_window=200, maxit=5000)
     assert rel(r["B"], orc["B"]) <= tol_b
     # the excluded coefficients are zero
     for i, f in enumerate(p.free):
