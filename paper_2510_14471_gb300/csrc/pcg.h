@@ -48,14 +48,17 @@ struct IterPlan {
 // Shared-memory layout of the tensor-core step kernels (byte offsets); pass 0
 // stages g and u tiles and keeps the S tile, pass 1 stages one u tile and NSG
 // g tiles and keeps the (Q C) tile.  The U operand of the MMA and the
-// accumulator live in tensor memory.
+// accumulator live in tensor memory.  Pass 0 keeps a staged row of G k
+// values in (G + 1) k floats: the pad puts the rows that one warp touches at
+// once on different banks.
 struct TcSmem {
   uint32_t om, vec, tile, q, total;
 };
+__host__ __device__ inline int tc_row_stride(int pass, int G, int KK) { return (pass == 0 ? G + 1 : G) * KK; }
 __host__ __device__ inline TcSmem tc_smem_layout(int pass, int G, int Gp, int KK, int np, int TQ, int NSQ, int NSG) {
   TcSmem L;
   const uint32_t TV = 128u / (uint32_t)KK;
-  const uint32_t tile_bytes = TV * (uint32_t)G * KK * 4u;
+  const uint32_t tile_bytes = TV * (uint32_t)tc_row_stride(pass, G, KK) * 4u;
   uint32_t off = 128;   // mbarriers (at most 16)
   L.om = off;
   off += 2u * Gp * Gp * 4u;

@@ -159,8 +159,9 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   const TcSmem L = tc_smem_layout(0, G, Gp, KK, np, TQ, NSQ, 0);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
   float* Bhi = reinterpret_cast<float*>(smraw + L.om);
+  const int GKP = tc_row_stride(0, G, KK);   // shared-memory row stride of the staged tiles
   float* gs = reinterpret_cast<float*>(smraw + L.vec);
-  float* us = gs + TV * G * KK;
+  float* us = gs + TV * GKP;
   float* Ss = reinterpret_cast<float*>(smraw + L.tile);   // S of the tile being projected
   float* qring = reinterpret_cast<float*>(smraw + L.q);
   __shared__ double red[16 * 16];
@@ -189,6 +190,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   // none, issues the MMAs and the vector copies meanwhile
   const int pwarps = (nq + 31) >> 5;
   const int issuer = pwarps < kTcThreads / 32 ? kTcThreads - 32 : 0;
+  const int iwarp = issuer >> 5;   // its warp issues the row copies, lane by lane
   if (tid == 0) {
     for (int q = 0; q < 2 + NSQ; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
@@ -207,14 +209,21 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   int vec_issued = 0, q_issued = 0, q_used = 0;   // (bookkeeping of the issuing threads)
   bool mma_pending = false;
   int mma_count = 0;
+  // (all lanes of the issuing warp) the g and u rows of a tile, one row per lane
   auto issue_vec = [&](int tile) {
     const int64_t row0 = r0 + (int64_t)tile * TV;
     const int tr = (int)((r1 - row0) < TV ? (r1 - row0) : TV);
-    const uint32_t bytes = (uint32_t)(tr * GK * sizeof(float));
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[0], 2 * bytes);
-    tma_load_1d(gs, g + row0 * GK, bytes, &bars[0]);
-    tma_load_1d(us, u + row0 * GK, bytes, &bars[0]);
+    const uint32_t rb = (uint32_t)(GK * sizeof(float));
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bars[0], 2u * (uint32_t)tr * rb);
+    }
+    __syncwarp();
+    if (lane < tr) {
+      fence_proxy_async_smem();
+      tma_load_1d(gs + lane * GKP, g + (row0 + lane) * GK, rb, &bars[0]);
+      tma_load_1d(us + lane * GKP, u + (row0 + lane) * GK, rb, &bars[0]);
+    }
   };
   auto issue_q = [&](int s) {
     const int slot = s % NSQ;
@@ -225,7 +234,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
     mbar_arrive_expect_tx(&bars[2 + slot], bytes);
     tma_load_1d(qring + (int64_t)slot * TQ * np, Q + row0 * np, bytes, &bars[2 + slot]);
   };
-  if (tid == issuer && ntiles > 0) issue_vec(vec_issued++);
+  if (warp == iwarp && ntiles > 0) issue_vec(vec_issued++);
   if (tid == 0)
     for (; q_issued < NSQ && q_issued < nsub; ++q_issued) issue_q(q_issued);
   const int r = 32 * (warp & 3) + lane;   // MMA row of this thread: (t_r, j_r)
@@ -244,39 +253,61 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   for (int it = 0; it <= ntiles; ++it) {
     const int64_t row0 = r0 + (int64_t)it * TV;
     const int tr = it < ntiles ? (int)((r1 - row0) < TV ? (r1 - row0) : TV) : 0;
-    float un[HB];
     if (it < ntiles) {
-      // E: u = g + mu u on the live columns, over the staged u; row r of the A operand
+      // E: u = g + mu u on the live columns, over the staged u; row r of the A
+      // operand.  Eight columns at a time: the loads of a chunk are issued
+      // before its stores, which write the same tile.
       lead_wait(&bars[0], it & 1, &abort_s, st.err);
       __syncthreads();
       if (abort_s) break;
       const bool rowok = t_r < tr;
 #pragma unroll
-      for (int c = 0; c < HB; ++c) {
-        const int h = hb + c;
-        float v = 0.f;
-        if (rowok && h < G) {
-          const int e = (t_r * G + h) * KK + j_r;
-          const float uo = us[e];
-          v = act_j ? gs[e] + mu_j * uo : uo;
-          if (act_j) us[e] = v;
-          if (snap_j) wbest[row0 * GK + e] = w[row0 * GK + e];   // the w whose c is a new quarter-low
+      for (int c0 = 0; c0 < HB; c0 += 8) {
+        float uo[8], gv[8], v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int h = hb + c0 + c;
+          const bool ok = rowok && h < G;
+          const int es = t_r * GKP + h * KK + j_r;
+          uo[c] = ok ? us[es] : 0.f;
+          gv[c] = ok ? gs[es] : 0.f;
         }
-        un[c] = v;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = act_j ? gv[c] + mu_j * uo[c] : uo[c];
+        if (act_j && rowok) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (hb + c0 + c < G) us[t_r * GKP + (hb + c0 + c) * KK + j_r] = v[c];
+        }
+        if (snap_j && rowok) {   // the w whose c is a new quarter-low
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int h = hb + c0 + c;
+            if (h < G) {
+              const int64_t e = row0 * GK + (t_r * G + h) * KK + j_r;
+              wbest[e] = w[e];
+            }
+          }
+        }
+        store_a_split_tmem<8>(trow, hb + c0, v);
       }
-      store_a_split_tmem<HB>(trow, hb, un);
       tmem_st_wait();
       fence_proxy_async_smem();   // the staged u is written back by a bulk copy
       tc_fence_before();
       __syncthreads();
-      if (tid == issuer) {
-        tc_fence_after();
-        issue_sigma_mma<Gp>(tmem, Bhi, &bars[1]);
+      if (warp == iwarp) {
+        if (lane == 0) {
+          tc_fence_after();
+          issue_sigma_mma<Gp>(tmem, Bhi, &bars[1]);
+        }
         mma_pending = true;
         ++mma_count;
-        tma_store_1d(u + row0 * GK, us, (uint32_t)(tr * GK * sizeof(float)));
-        bulk_commit();
-        bulk_wait_read_all();   // the stage may be refilled once the store has read it
+        if (lane < tr) {   // one row of u per lane
+          tma_store_1d(u + (row0 + lane) * GK, us + lane * GKP, (uint32_t)(GK * sizeof(float)));
+          bulk_commit();
+          bulk_wait_read_all();   // the stage may be refilled once the store has read it
+        }
+        __syncwarp();
         if (vec_issued < ntiles) issue_vec(vec_issued++);
       }
     }
@@ -299,7 +330,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
           const float* qs = qring + (int64_t)slot * TQ * np + 4 * tid;
           for (int rr = 0; rr < tq; ++rr) {
             const float4 qv = *reinterpret_cast<const float4*>(qs + (int64_t)rr * np);
-            const float4* sp = reinterpret_cast<const float4*>(Ss + ((tl0 + rr) * G + blk) * KK);
+            const float4* sp = reinterpret_cast<const float4*>(Ss + (tl0 + rr) * GKP + blk * KK);
             const float qc[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
             for (int a = 0; a < KK / 4; ++a) {
@@ -332,20 +363,30 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
       if (abort_s) break;
       if (tid == issuer) mma_pending = false;
       tc_fence_after();
-      float sv[HB];
-      load_s<HB, Gp>(trow, hb, sv);
-      if (t_r < tr) {
-        float dl = 0.f;
+      // S = the two accumulator halves; u = A_hi + A_lo read back from tensor
+      // memory (the split is exact), so u needs no registers across the step
+      float dl = 0.f;
 #pragma unroll
-        for (int c = 0; c < HB; ++c) {
-          const int h = hb + c;
-          if (h < G) {
-            dl += un[c] * sv[c];
-            Ss[(t_r * G + h) * KK + j_r] = sv[c];
+      for (int c0 = 0; c0 < HB; c0 += 8) {
+        float sv[8], s1[8], ah[8], al[8];
+        tmem_ld<8>(trow + (uint32_t)(hb + c0), sv);
+        tmem_ld<8>(trow + (uint32_t)(Gp + hb + c0), s1);
+        tmem_ld<8>(trow + kColAhi + (uint32_t)(hb + c0), ah);
+        tmem_ld<8>(trow + kColAlo + (uint32_t)(hb + c0), al);
+        tmem_ld_wait();
+        if (t_r < tr) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int h = hb + c0 + c;
+            if (h < G) {
+              const float sc = sv[c] + s1[c];
+              dl += (ah[c] + al[c]) * sc;
+              Ss[t_r * GKP + h * KK + j_r] = sc;
+            }
           }
         }
-        dsum += (double)dl;   // d = u^T S: per-tile float partials added in float64
       }
+      if (t_r < tr) dsum += (double)dl;   // d = u^T S: per-tile float partials added in float64
       tc_fence_before();
       __syncthreads();
     }
@@ -369,7 +410,7 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
               make_float4(acc[c][4 * a], acc[c][4 * a + 1], acc[c][4 * a + 2], acc[c][4 * a + 3]);
     }
   }
-  if (tid == issuer) bulk_wait_all();   // the stores of u have completed
+  if (warp == iwarp) bulk_wait_all();   // the stores of u (one per lane) have completed
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
