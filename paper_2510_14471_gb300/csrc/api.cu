@@ -296,7 +296,12 @@ glm_sur_status make_plan(glm_sur_ctx* h, int k, bool is_double, IterPlan& p) {
       int tq2 = 0, nsq2 = 0, tq1 = 0, nsq1 = 0;
       const bool ok2 = pick_q(1, 2, tq2, nsq2), ok1 = pick_q(1, 1, tq1, nsq1);
       const bool okb = ok2 || ok1;
-      if (ok2 && (tq2 * nsq2 >= TV || !ok1)) {
+      if (tc_smem_layout(1, gm.G, p.tc_gp, k, gm.np, TV, 2, 1).total <= tc_budget) {
+        // one Q sub-tile per vector tile, two in flight, one staged g tile:
+        // the fastest ring measured at G = 64, k = 16 (pass B 0.143 ms against
+        // 0.152 with two g tiles and half-height Q sub-tiles)
+        p.tc_nsg = 1; p.tc_tq_b = TV; p.tc_nsq_b = 2;
+      } else if (ok2 && (tq2 * nsq2 >= TV || !ok1)) {
         p.tc_nsg = 2; p.tc_tq_b = tq2; p.tc_nsq_b = nsq2;
       } else if (ok1) {
         p.tc_nsg = 1; p.tc_tq_b = tq1; p.tc_nsq_b = nsq1;
