@@ -904,16 +904,16 @@ def run_var(args, rank, world, local, pg):
         yv = torch.as_tensor(p.y_vec(), device=dev)
         for name, make, call, to_b in (
                 ("mvrglm_K1", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="scaled", tol=1e-10,
-                                                stagnation_window=200, maxit=5000, device=dev),
+                                                stagnation_window=1000, maxit=5000, device=dev),
                  lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
                 ("mvrglm_K2", lambda: GlmMvrglm(p.Z0, p.Omega0, p.C_list, precond="diag", tol=1e-10,
-                                                stagnation_window=200, maxit=5000, device=dev),
+                                                stagnation_window=1000, maxit=5000, device=dev),
                  lambda h: h.solve(Yd), lambda r: r.b[:, :, 0].cpu().numpy()),
                 ("pcg_aug_K1", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="scaled", tol=1e-10,
-                                              stagnation_window=200, maxit=5000, device=dev),
+                                              stagnation_window=1000, maxit=5000, device=dev),
                  lambda h: h.solve(yv), None),
                 ("pcg_aug_K2", lambda: GlmSur(p.free_blocks(), p.Omega0, precond="diag", tol=1e-10,
-                                              stagnation_window=200, maxit=5000, device=dev),
+                                              stagnation_window=1000, maxit=5000, device=dev),
                  lambda h: h.solve(yv), None),
                 ("pcg_ne", lambda: GlmSur(p.free_blocks(), p.Omega0, tol=1e-10, maxit=20000, device=dev),
                  lambda h: h.solve_ne(yv), None)):
