@@ -18,17 +18,18 @@ def args(**kw):
 
 
 def test_traffic_of_each_step_kernel_is_read_from_the_profile_summary():
-    for kernel in ("sigma_step", "proj_partial", "proj_update"):
+    for kernel in ("pass_a", "pass_b"):
         t = bench.ncu_traffic(args(), kernel)
         assert isinstance(t, int) and t > 10 ** 8, (kernel, t)
-    # the Sigma step moves about its algorithmic bytes (read g, u, w; write u, w, S)
-    alg = 6 * 4 * 20000 * 64 * 16
-    assert 0.5 * alg < bench.ncu_traffic(args(), "sigma_step") < 1.5 * alg
+    # pass B moves about its algorithmic bytes (read u, g, w, Q; write g, w)
+    mk, Mn = 20000 * 64 * 16, 20000 * 1234
+    alg = 4 * (Mn + 5 * mk)
+    assert 0.5 * alg < bench.ncu_traffic(args(), "pass_b") < 1.5 * alg
 
 
 def test_no_traffic_without_a_matching_summary():
-    assert bench.ncu_traffic(args(precision="fp64"), "sigma_step") is None
-    assert bench.ncu_traffic(args(M=12345), "sigma_step") is None
+    assert bench.ncu_traffic(args(precision="fp64"), "pass_b") is None
+    assert bench.ncu_traffic(args(M=12345), "pass_b") is None
     assert bench.ncu_traffic(args(), "reduce") is None
 
 
