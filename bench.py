@@ -213,7 +213,7 @@ def run_extras(timeout_s=420):
             continue
         keep = ["value", "unit", "ms_per_step", "dtype", "config", "roofline", "roofline_iter", "e2e", "gpu_launches",
                 "clocks", "rel_err_sampled", "rel_err", "status_counts", "steps_per_instance", "iters_max", "k1",
-                "grad_err", "b_err", "steps", "models"]
+                "grad_err", "b_err", "steps", "models", "row_reduced"]
         out[w] = {k2: line[k2] for k2 in keep if k2 in line}
         out[w]["wall_s"] = time.perf_counter() - t0
     return out
@@ -602,6 +602,35 @@ def run_batched(args, rank, world, local, pg):
         cpu = {"value": nrun / dt, "unit": "instance solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the float64 reference PCG of the oracle (k={k}, tol 1e-12) on the first {nrun} "
                          f"instances, {dt:.1f} s"}
+    # the same batch on the row-reduced instances (Remark rem:reduction: every
+    # instance with M >= 2n solved on its n rotated rows)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    btr = GlmSurBatch([(q.X_blocks, q.Omega) for q in probs], reduce_rows=True, device=dev)
+    torch.cuda.synchronize()
+    setup_r_ms = (time.perf_counter() - t0) * 1e3
+    br = torch.empty(nb, dtype=torch.float64, device=dev)
+    itr = torch.zeros(count * k, dtype=torch.int32, device=dev)
+    rrr = torch.zeros(count * k, dtype=torch.float64, device=dev)
+
+    def solve_r():
+        L.glm_sur_batch_solve(btr.handle, Y.data_ptr(), k, br.data_ptr(), itr.data_ptr(), rrr.data_ptr(), stream)
+
+    solve_r()
+    torch.cuda.synchronize()
+    ms_r, _ = timed(solve_r, args.steps, args.warmup, local, pg)
+    status_r = np.array(L.glm_sur_batch_get_status(btr.handle, count * k))
+    ms_r, value_r = aggregate(ms_r, pg, world, dev)
+    bsr, errs_r = br.cpu().numpy(), {}
+    for j in (0, 1, 777, 2047):
+        bj = bsr[offs[j]:offs[j + 1]].reshape(k, bt.n[j]).T
+        errs_r[j] = rel_err(bj, O.sur_gls_structured(probs[j].X_blocks, probs[j].Omega, probs[j].Y))
+    row_reduced = {"value": value_r * count, "unit": "instance solves/s", "ms": ms_r, "setup_ms": setup_r_ms,
+                   "rel_err_sampled": errs_r,
+                   "status_counts": {int(v): int(c) for v, c in zip(*np.unique(status_r, return_counts=True))},
+                   "steps_max": int(itr.view(count, k).max().item()),
+                   "note": "every instance with M >= 2n on its n rows; one float64 product Q_W^T Y per instance"}
+    btr.close()
     if rank == 0:
         line = base_line(args, world, METRIC, "batched-2048-uneven-k8 (G~U{2..12}, M~U{200..4000}, "
                          "n_i~U{2..10}, Omega Wishart(G,G+4)/trace)", value, "instance solves/s", ms, "f32+f64",
@@ -616,6 +645,7 @@ def run_batched(args, rank, world, local, pg):
                          "frac": ach / hbm, "traffic": None, "peak_source": src, "algorithmic_bytes": alg,
                          "ms": ms, "note": "lower bound of the work: steps per instance = max over its columns"},
             "cpu_baseline": cpu,
+            "row_reduced": row_reduced,
             "e2e": {"value": world * count / float(np.mean(e2e)), "unit": "instance solves/s",
                     "h2d_bytes_per_step": int(Y.numel() * 8), "d2h_bytes_per_step": int(nb * 8)},
             "gpu_launches": int(launches), "clocks": clocks})

@@ -375,7 +375,13 @@ typedef struct glm_sur_batch_ctx* glm_sur_batch_t;
  *   Omega : DEVICE, the instances' Omega_j (G_j x G_j column-major) one after
  *           another.
  *   opts  : tol (float64 residual ||P(y - Sigma w)|| / ||P y||), inner_tol,
- *           max_refine are used; may be NULL.  The float64 residual of a
+ *           max_refine and reduce_rows are used; may be NULL.  reduce_rows = 1
+ *           solves every instance with M_j >= 2 n_j on the n_j rows of its
+ *           projection onto range([X_1 ... X_G]) (Remark rem:reduction: Q_W
+ *           by Cholesky QR twice at setup, one float64 product Q_W^T Y_j per
+ *           instance and solve; tol and relres then refer to the reduced
+ *           system); when some W_j has no full column rank the whole batch
+ *           is kept unreduced.  The float64 residual of a
  *           refined solve settles at a few 1e-13 on instances of this size,
  *           so a tol below that ends in GLM_SUR_NOT_CONVERGED after
  *           max_refine refinement steps with b still at full accuracy.

@@ -12,6 +12,8 @@
 #include "glm_sur.h"
 #include "internal.h"
 #include "pcg.h"
+#include "reduce.h"
+#include "rglm.h"
 
 using namespace glmsur;
 
@@ -43,6 +45,19 @@ struct glm_sur_batch_ctx {
   const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int graph_k = 0;
   int64_t launches = 0;
+  // row reduction (Remark rem:reduction, opts.reduce_rows): the solves run on
+  // `inner`, the batch of the reduced instances (n_j rows per equation);
+  // reduced instance j keeps Q_W (M_j x n_j column-major) at qw_off[j]
+  glm_sur_batch_ctx* inner = nullptr;
+  std::vector<int> red;                 // 1: instance reduced
+  std::vector<int64_t> qw_off, y_off, yr_off;
+  int64_t y_rows = 0, yr_rows = 0;      // sum G M, sum G M'
+  double* qw = nullptr;
+  double* yred = nullptr;
+  int yred_k = 0;
+  DgemmProblem* d_rot = nullptr;        // rotation problems of the last (Y, k)
+  const double* rot_y = nullptr;
+  int rot_k = 0, rot_count = 0, rot_tiles = 0;
 };
 
 namespace {
@@ -111,6 +126,168 @@ static cudaError_t write_work_order(glm_sur_batch_ctx* h, int k, const std::vect
   return cudaMemcpy(h->d_insts, insts.data(), sizeof(BatchInst) * h->count, cudaMemcpyHostToDevice);
 }
 
+// Remark rem:reduction for every instance with M_j >= 2 n_j: Q_W (M_j x n_j
+// orthonormal, range(Q_W) = range(W_j), W_j = [X_1 ... X_G]) by Cholesky QR
+// twice and R_W = L2^T L1^T; the reduced instance has the regressor blocks
+// R_W[:, block i] (n_j rows) and the responses Q_W^T y_i.  The products of
+// all instances run as one batched launch per stage; the Cholesky
+// factorisations and triangular inverses are one-CTA launches per instance.
+// Returns GLM_SUR_RANK_DEFICIENT when some W_j has no full column rank (the
+// caller then keeps the batch whole).
+static glm_sur_status batch_setup_reduced(glm_sur_batch_t* out, int count, const int* G, const int* M,
+                                          const int* n_i, const double* X, const double* Omega,
+                                          const glm_sur_opts& o, cudaStream_t s) {
+  glm_sur_batch_ctx* h = new glm_sur_batch_ctx();
+  h->count = count;
+  h->opts = o;
+  std::vector<int> n(count), Mr(count);
+  std::vector<int64_t> x_off(count), xr_off(count), nn_off(count);
+  int64_t xo = 0, xro = 0, qwo = 0, nb = 0, nno = 0;
+  for (int j = 0; j < count; ++j) {
+    int nj = 0;
+    for (int i = 0; i < G[j]; ++i) nj += n_i[nb + i];
+    nb += G[j];
+    n[j] = nj;
+    const bool r = M[j] >= 2 * nj && nj <= kMaxReducedCols;
+    h->red.push_back(r ? 1 : 0);
+    Mr[j] = r ? nj : M[j];
+    x_off[j] = xo;
+    xr_off[j] = xro;
+    nn_off[j] = nno;
+    h->qw_off.push_back(r ? qwo : -1);
+    h->y_off.push_back(h->y_rows);
+    h->yr_off.push_back(h->yr_rows);
+    xo += (int64_t)M[j] * nj;
+    xro += (int64_t)Mr[j] * nj;
+    if (r) {
+      qwo += (int64_t)M[j] * nj;
+      nno += (int64_t)nj * nj;
+    }
+    h->y_rows += (int64_t)G[j] * M[j];
+    h->yr_rows += (int64_t)G[j] * Mr[j];
+  }
+  double *xr = nullptr, *G1 = nullptr, *Li1 = nullptr, *G2 = nullptr, *Li2 = nullptr, *Q1 = nullptr;
+  int* flags = nullptr;
+  DgemmProblem* dprob = nullptr;
+  auto release = [&]() {
+    bfree(xr); bfree(G1); bfree(Li1); bfree(G2); bfree(Li2); bfree(Q1); bfree(flags); bfree(dprob);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_last_error(e, what, __FILE__, __LINE__);
+    release();
+    bfree(h->qw);
+    bfree(h->d_rot);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? GLM_SUR_OOM : GLM_SUR_CUDA_ERROR;
+  };
+  cudaError_t e;
+#define RTRY(x) if ((e = (x)) != cudaSuccess) return fail(e, #x)
+  RTRY(balloc(&xr, (size_t)xro));
+  RTRY(balloc(&h->qw, (size_t)qwo));
+  RTRY(balloc(&G1, (size_t)nno)); RTRY(balloc(&Li1, (size_t)nno));
+  RTRY(balloc(&G2, (size_t)nno)); RTRY(balloc(&Li2, (size_t)nno));
+  RTRY(balloc(&Q1, (size_t)qwo));
+  RTRY(balloc(&flags, (size_t)count));
+  RTRY(balloc(&dprob, (size_t)count));
+  RTRY(balloc(&h->d_rot, (size_t)count));
+  RTRY(cudaMemsetAsync(flags, 0, sizeof(int) * count, s));
+  std::vector<DgemmProblem> pr;
+  // one stage of products, one problem per reduced instance
+  auto stage = [&](auto make) -> cudaError_t {
+    pr.clear();
+    int tiles = 0;
+    for (int j = 0; j < count; ++j)
+      if (h->red[j]) {
+        pr.push_back(make(j));
+        tiles = std::max(tiles, dgemm_tiles(pr.back().m, pr.back().n));
+      }
+    if (pr.empty()) return cudaSuccess;
+    cudaError_t ce = cudaMemcpyAsync(dprob, pr.data(), sizeof(DgemmProblem) * pr.size(), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return ce;
+    launch_dgemm_batched(dprob, (int)pr.size(), tiles, s);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);   // `pr` is reused by the next stage
+    h->launches += 1;
+    return ce;
+  };
+  // per-instance Cholesky and inverse of a stage's n x n Gram matrices
+  auto factor = [&](double* Gm, double* Li) -> cudaError_t {
+    for (int j = 0; j < count; ++j) {
+      if (!h->red[j]) continue;
+      const int nj = n[j];
+      const double piv_tol = 64.0 * nj * 2.220446049250313e-16;   // below: W treated as rank deficient
+      cudaError_t ce = cholesky_lower(nj, Gm + nn_off[j], flags + j, piv_tol, s);
+      if (ce != cudaSuccess) return ce;
+      launch_zero_upper(nj, Gm + nn_off[j], s);
+      ce = launch_tri_inverse(nj, Gm + nn_off[j], Li + nn_off[j], s);
+      if (ce != cudaSuccess) return ce;
+      h->launches += 3;
+    }
+    return cudaGetLastError();
+  };
+  for (int j = 0; j < count; ++j)
+    if (!h->red[j])
+      RTRY(cudaMemcpyAsync(xr + xr_off[j], X + x_off[j], sizeof(double) * (size_t)M[j] * n[j],
+                           cudaMemcpyDeviceToDevice, s));
+  // W^T W = L1 L1^T ;  Q1 = W L1^-T ;  Q1^T Q1 = L2 L2^T ;  Q = Q1 L2^-T ;  R_W = L2^T L1^T
+  RTRY(stage([&](int j) {
+    const int64_t Mj = M[j];
+    const double* W = X + x_off[j];
+    return DgemmProblem{n[j], n[j], Mj, W, Mj, 1, W, 1, Mj, G1 + nn_off[j], n[j], 1};
+  }));
+  RTRY(factor(G1, Li1));
+  RTRY(stage([&](int j) {
+    const int64_t Mj = M[j];
+    return DgemmProblem{(int)Mj, n[j], n[j], X + x_off[j], 1, Mj, Li1 + nn_off[j], 1, n[j],
+                        Q1 + h->qw_off[j], 1, Mj};
+  }));
+  RTRY(stage([&](int j) {
+    const int64_t Mj = M[j];
+    const double* A = Q1 + h->qw_off[j];
+    return DgemmProblem{n[j], n[j], Mj, A, Mj, 1, A, 1, Mj, G2 + nn_off[j], n[j], 1};
+  }));
+  RTRY(factor(G2, Li2));
+  RTRY(stage([&](int j) {
+    const int64_t Mj = M[j];
+    return DgemmProblem{(int)Mj, n[j], n[j], Q1 + h->qw_off[j], 1, Mj, Li2 + nn_off[j], 1, n[j],
+                        h->qw + h->qw_off[j], 1, Mj};
+  }));
+  RTRY(stage([&](int j) {
+    return DgemmProblem{n[j], n[j], n[j], G2 + nn_off[j], 1, n[j], G1 + nn_off[j], 1, n[j], xr + xr_off[j], 1, n[j]};
+  }));
+  std::vector<int> hflags(count, 0);
+  RTRY(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+  RTRY(cudaStreamSynchronize(s));
+  for (int j = 0; j < count; ++j)
+    if (hflags[j]) {
+      release();
+      bfree(h->qw);
+      bfree(h->d_rot);
+      delete h;
+      return GLM_SUR_RANK_DEFICIENT;
+    }
+  glm_sur_opts so = o;
+  so.reduce_rows = 0;
+  glm_sur_batch_t inner = nullptr;
+  glm_sur_status rc = glm_sur_batch_setup(&inner, count, G, Mr.data(), n_i, xr, Omega, &so,
+                                          reinterpret_cast<glm_sur_stream_t>(s));
+  cudaStreamSynchronize(s);
+  release();
+  if (rc != GLM_SUR_OK) {
+    bfree(h->qw);
+    bfree(h->d_rot);
+    delete h;
+    return rc;
+  }
+#undef RTRY
+  h->inner = inner;
+  h->G.assign(G, G + count);
+  h->M.assign(M, M + count);
+  h->n = n;
+  *out = h;
+  return GLM_SUR_OK;
+}
+
 extern "C" {
 
 glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G, const int* M, const int* n_i,
@@ -122,6 +299,20 @@ glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G
   glm_sur_default_opts(&o);
   if (opts) o = *opts;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.reduce_rows) {
+    // validate the instances first: the reduced setup assumes their sizes
+    int64_t nb = 0;
+    for (int j = 0; j < count; ++j) {
+      if (G[j] < 1 || G[j] > kBatchMaxG || M[j] < 1) return GLM_SUR_INVALID_ARG;
+      for (int i = 0; i < G[j]; ++i)
+        if (n_i[nb + i] < 1 || n_i[nb + i] > kBatchMaxCols || n_i[nb + i] > M[j]) return GLM_SUR_INVALID_ARG;
+      nb += G[j];
+    }
+    glm_sur_status rr = batch_setup_reduced(out, count, G, M, n_i, X, Omega, o, s);
+    if (rr != GLM_SUR_RANK_DEFICIENT) return rr;
+    // some W_j without full column rank: the batch is kept whole
+    o.reduce_rows = 0;
+  }
   glm_sur_batch_ctx* h = new glm_sur_batch_ctx();
   h->count = count;
   h->opts = o;
@@ -221,6 +412,7 @@ glm_sur_status glm_sur_batch_setup(glm_sur_batch_t* out, int count, const int* G
 }
 
 glm_sur_status glm_sur_batch_get_setup_status(glm_sur_batch_t h) {
+  if (h && h->inner) return glm_sur_batch_get_setup_status(h->inner);
   if (!h) return GLM_SUR_INVALID_ARG;
   int flags = 0;
   GS_CUDA_TRY(cudaMemcpy(&flags, h->setup_flags, sizeof(int), cudaMemcpyDeviceToHost));
@@ -233,8 +425,48 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
                                    double* relres, glm_sur_stream_t stream) {
   if (!h || !Y || !b) return GLM_SUR_INVALID_ARG;
   if (k != 1 && k != 2 && k != 4 && k != 8) return GLM_SUR_INVALID_ARG;
-  if (h->maxNq * k > kBatchMaxPairs) return GLM_SUR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (h->inner) {
+    // Remark rem:reduction: y' = Q_W^T y per reduced instance (one float64
+    // product of its G_j k columns), the other instances copied; then the
+    // batch of the reduced instances
+    if (k > h->yred_k) {
+      GS_CUDA_TRY(cudaStreamSynchronize(s));   // an earlier solve may still read the old buffer
+      bfree(h->yred);
+      h->yred_k = 0;
+      GS_CUDA_TRY(balloc(&h->yred, (size_t)h->yr_rows * k));
+      h->yred_k = k;
+      h->rot_y = nullptr;                      // the rotation problems point at the old buffer
+    }
+    if (Y != h->rot_y || k != h->rot_k) {
+      // the rotation problems of this (Y, k): one batched float64 launch per solve
+      std::vector<DgemmProblem> pr;
+      int tiles = 0;
+      for (int j = 0; j < h->count; ++j) {
+        if (!h->red[j]) continue;
+        const int64_t Mj = h->M[j];
+        pr.push_back(DgemmProblem{h->n[j], h->G[j] * k, Mj, h->qw + h->qw_off[j], Mj, 1, Y + h->y_off[j] * k, 1, Mj,
+                                  h->yred + h->yr_off[j] * k, 1, h->n[j]});
+        tiles = std::max(tiles, dgemm_tiles(pr.back().m, pr.back().n));
+      }
+      if (!pr.empty())
+        GS_CUDA_TRY(cudaMemcpy(h->d_rot, pr.data(), sizeof(DgemmProblem) * pr.size(), cudaMemcpyHostToDevice));
+      h->rot_y = Y;
+      h->rot_k = k;
+      h->rot_count = (int)pr.size();
+      h->rot_tiles = tiles;
+    }
+    launch_dgemm_batched(h->d_rot, h->rot_count, h->rot_tiles, s);
+    h->launches += 1;
+    for (int j = 0; j < h->count; ++j)
+      if (!h->red[j])
+        GS_CUDA_TRY(cudaMemcpyAsync(h->yred + h->yr_off[j] * k, Y + h->y_off[j] * k,
+                                    sizeof(double) * (size_t)h->G[j] * h->M[j] * k, cudaMemcpyDeviceToDevice, s));
+    GS_CUDA_TRY(cudaGetLastError());
+    h->last_k = k;
+    return glm_sur_batch_solve(h->inner, h->yred, k, b, iters, relres, stream);
+  }
+  if (h->maxNq * k > kBatchMaxPairs) return GLM_SUR_INVALID_ARG;
   if (k > h->kcap) {
     free_solve(h);
     const size_t nv = (size_t)h->v_rows * k;
@@ -337,6 +569,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
 }
 
 glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status) {
+  if (h && h->inner) return glm_sur_batch_get_status(h->inner, status);
   if (!h || !status || h->last_k < 1) return GLM_SUR_INVALID_ARG;
   GS_CUDA_TRY(cudaDeviceSynchronize());
   GS_CUDA_TRY(cudaMemcpy(status, h->status, sizeof(int) * h->count * h->last_k, cudaMemcpyDeviceToHost));
@@ -350,6 +583,7 @@ glm_sur_status glm_sur_batch_get_status(glm_sur_batch_t h, int* status) {
 }
 
 glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* cycles) {
+  if (h && h->inner) return glm_sur_batch_get_work(h->inner, steps, cycles);
   if (!h || (!steps && !cycles)) return GLM_SUR_INVALID_ARG;
   if (!h->steps_d) return GLM_SUR_INVALID_ARG;   // no solve yet
   GS_CUDA_TRY(cudaDeviceSynchronize());
@@ -359,16 +593,28 @@ glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* 
 }
 
 int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms) {
+  if (h && h->inner) return glm_sur_batch_tile(h->inner, tune_ms);
   if (!h) return -1;
   if (tune_ms)
     for (int t = 0; t < 3; ++t) tune_ms[t] = h->tune_ms[t];
   return h->tile;
 }
 
-int64_t glm_sur_batch_launch_count(glm_sur_batch_t h) { return h ? h->launches : -1; }
+int64_t glm_sur_batch_launch_count(glm_sur_batch_t h) {
+  if (!h) return -1;
+  return h->launches + (h->inner ? glm_sur_batch_launch_count(h->inner) : 0);
+}
 
 void glm_sur_batch_destroy(glm_sur_batch_t h) {
   if (!h) return;
+  if (h->inner) {
+    glm_sur_batch_destroy(h->inner);
+    bfree(h->qw);
+    bfree(h->yred);
+    bfree(h->d_rot);
+    delete h;
+    return;
+  }
   cudaDeviceSynchronize();
   free_solve(h);
   bfree(h->q64); bfree(h->q32); bfree(h->R); bfree(h->om64); bfree(h->om32);

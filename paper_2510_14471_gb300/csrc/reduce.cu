@@ -18,13 +18,13 @@ namespace {
 
 constexpr int kTM = 64, kTN = 64, kTK = 16;   // output tile and depth step of the float64 product
 
-// 256 threads, 4 x 4 outputs each; A and B tiles staged in shared memory.
-__global__ void __launch_bounds__(256)
-k_dgemm(int m, int n, int64_t kdim, const double* __restrict__ A, int64_t ars, int64_t acs,
-        const double* __restrict__ B, int64_t brs, int64_t bcs, double* __restrict__ C, int64_t crs, int64_t ccs) {
+// One kTM x kTN output tile at (i0, j0): 256 threads, 4 x 4 outputs each; A
+// and B tiles staged in shared memory.
+__device__ __forceinline__ void dgemm_tile(int i0, int j0, int m, int n, int64_t kdim, const double* __restrict__ A,
+                                           int64_t ars, int64_t acs, const double* __restrict__ B, int64_t brs,
+                                           int64_t bcs, double* __restrict__ C, int64_t crs, int64_t ccs) {
   __shared__ double As[kTK][kTM + 1];
   __shared__ double Bs[kTK][kTN + 1];
-  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4] = {};
   for (int64_t p0 = 0; p0 < kdim; p0 += kTK) {
@@ -68,6 +68,23 @@ k_dgemm(int m, int n, int64_t kdim, const double* __restrict__ A, int64_t ars, i
   }
 }
 
+__global__ void __launch_bounds__(256)
+k_dgemm(int m, int n, int64_t kdim, const double* __restrict__ A, int64_t ars, int64_t acs,
+        const double* __restrict__ B, int64_t brs, int64_t bcs, double* __restrict__ C, int64_t crs, int64_t ccs) {
+  dgemm_tile(blockIdx.y * kTM, blockIdx.x * kTN, m, n, kdim, A, ars, acs, B, brs, bcs, C, crs, ccs);
+}
+
+// grid (tiles, problems): CTA (t, q) computes tile t of problem q (row-major
+// over its tiles), or nothing when problem q has fewer tiles
+__global__ void __launch_bounds__(256) k_dgemm_batched(const DgemmProblem* __restrict__ probs) {
+  const DgemmProblem pr = probs[blockIdx.y];
+  const int tn = (int)ceil_div(pr.n, kTN), tm = (int)ceil_div(pr.m, kTM);
+  const int t = blockIdx.x;
+  if (pr.m < 1 || pr.n < 1 || t >= tm * tn) return;
+  dgemm_tile((t / tn) * kTM, (t % tn) * kTN, pr.m, pr.n, pr.kdim, pr.A, pr.ars, pr.acs, pr.B, pr.brs, pr.bcs, pr.C,
+             pr.crs, pr.ccs);
+}
+
 // Column j of L^-1 (forward substitution L y = e_j; one CTA per column).
 __global__ void __launch_bounds__(256) k_tri_inverse_cols(int n, const double* __restrict__ L,
                                                           double* __restrict__ Linv) {
@@ -106,6 +123,13 @@ void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int6
                   int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(n, kTN), (unsigned)ceil_div(m, kTM));
   k_dgemm<<<grid, 256, 0, s>>>(m, n, kdim, A, ars, acs, B, brs, bcs, C, crs, ccs);
+}
+
+int dgemm_tiles(int m, int n) { return (int)(ceil_div(m, kTM) * ceil_div(n, kTN)); }
+
+void launch_dgemm_batched(const DgemmProblem* probs, int count, int max_tiles, cudaStream_t s) {
+  if (count < 1 || max_tiles < 1) return;
+  k_dgemm_batched<<<dim3((unsigned)max_tiles, (unsigned)count), 256, 0, s>>>(probs);
 }
 
 cudaError_t launch_tri_inverse(int n, const double* L, double* Linv, cudaStream_t s) {

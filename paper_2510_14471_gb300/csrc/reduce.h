@@ -14,6 +14,23 @@ namespace glmsur {
 void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int64_t acs, const double* B,
                   int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s);
 
+// One float64 product C = A B of a batch (layout as launch_dgemm).
+struct DgemmProblem {
+  int m, n;
+  int64_t kdim;
+  const double* A;
+  int64_t ars, acs;
+  const double* B;
+  int64_t brs, bcs;
+  double* C;
+  int64_t crs, ccs;
+};
+// Output tiles of an m x n product.
+int dgemm_tiles(int m, int n);
+// Every problem of `probs` (DEVICE array of count) in one launch; max_tiles =
+// the largest dgemm_tiles of them.  The problems' outputs must not overlap.
+void launch_dgemm_batched(const DgemmProblem* probs, int count, int max_tiles, cudaStream_t s);
+
 // Linv = L^-1 for a row-major lower-triangular n x n L (its strict upper
 // triangle is ignored); Linv row-major with zeros above the diagonal.
 cudaError_t launch_tri_inverse(int n, const double* L, double* Linv, cudaStream_t s);

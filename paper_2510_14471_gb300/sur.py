@@ -267,11 +267,13 @@ class GlmSurBatch:
     """Many independent SUR instances solved in one persistent launch.
 
     problems: list of (X_blocks, Omega) pairs (numpy or torch, float64).
+    reduce_rows: solve every instance with M >= 2 n on its n rotated rows
+    (Remark rem:reduction; tol then refers to the reduced system).
     tol defaults to 1e-12: the float64 residual of a refined batched solve
     settles at a few 1e-13, below which refinement steps buy nothing."""
 
     def __init__(self, problems, tol: float = 1e-12, inner_tol: float = 1e-5, max_refine: int = 8,
-                 device="cuda"):
+                 reduce_rows: bool = False, device="cuda"):
         self.device = torch.device(device)
         self.G = [len(xb) for xb, _ in problems]
         self.M = [int(xb[0].shape[0]) for xb, _ in problems]
@@ -287,6 +289,7 @@ class GlmSurBatch:
         self.opts.tol = tol
         self.opts.inner_tol = inner_tol
         self.opts.max_refine = max_refine
+        self.opts.reduce_rows = int(bool(reduce_rows))
         self._h = L.glm_sur_batch_setup(len(problems), self.G, self.M, self.n_i, self._X.data_ptr(),
                                         self._Om.data_ptr(), self.opts, torch.cuda.current_stream().cuda_stream)
 
