@@ -823,6 +823,7 @@ def run_differentiable(args, rank, world, local, pg):
     ms, clocks = timed(step, args.steps, args.warmup, local, pg)
     launches = (L.glm_sur_launch_count(h.handle) - l0) // (args.steps + args.warmup)
     ms, value = aggregate(ms, pg, world, dev)
+    iters_fb = (int(it_f.item()), int(it_b.item()))
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "cfg4_reference.json")))
     bb = b[0].cpu().numpy()
     err_b = float(np.linalg.norm(bb - np.asarray(gold["b"])) / np.linalg.norm(gold["b"]))
@@ -850,6 +851,28 @@ def run_differentiable(args, rank, world, local, pg):
         cpu = {"value": 1.0 / dt, "unit": "forward+adjoint/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the oracle's Kronecker-inverse GLS and adjoint (normal equations, float64), two calls, "
                          f"{dt:.1f} s"}
+    # the same forward + adjoint on the row-reduced model (Remark
+    # rem:reduction: 40000 rows per equation -> n; dL/dY = Q dL/dy')
+    hr = GlmSur(p.X_blocks, p.Omega, precision="fp32_refine", stagnation_window=1000, max_refine=20,
+                reduce_rows=True, device=dev)
+
+    def step_r():
+        L.glm_sur_solve(hr.handle, Ycm.data_ptr(), m, 1, b.data_ptr(), n, it_f.data_ptr(), rr.data_ptr(), stream)
+        torch.sub(b[0], tgt, out=gb[0]).mul_(2.0)
+        L.glm_sur_backward(hr.handle, gb.data_ptr(), n, 1, dY.data_ptr(), m, dO.data_ptr(), G, it_b.data_ptr(),
+                           rr.data_ptr(), stream)
+
+    ms_r, _ = timed(step_r, args.steps, args.warmup, local, pg)
+    ms_r, value_r = aggregate(ms_r, pg, world, dev)
+    bbr = b[0].cpu().numpy()
+    omr = dO.cpu().numpy().reshape(-1)[gold["dOmega_idx"]]
+    row_reduced = {"value": value_r, "unit": "forward+adjoint/s", "ms": ms_r,
+                   "rel_err_b": float(np.linalg.norm(bbr - np.asarray(gold["b"])) / np.linalg.norm(gold["b"])),
+                   "rel_err_dOmega_sampled": float(np.linalg.norm(omr - np.asarray(gold["dOmega_sym"])) /
+                                                   np.linalg.norm(gold["dOmega_sym"])),
+                   "iters_forward": int(it_f.item()), "iters_adjoint": int(it_b.item()),
+                   "note": f"every equation on its n = {n} rotated rows; float64 products Q^T y and Q dL/dy'"}
+    hr.close()
     # end to end: Y from the host, b, dL/dY and dL/dOmega back
     Y2 = torch.empty_like(Ycm)
     bh = torch.empty((1, n), dtype=torch.float64).pin_memory()
@@ -875,7 +898,8 @@ def run_differentiable(args, rank, world, local, pg):
                           "stagnation_window": 1000, "l2": "Q 287 MB f32 + 573 MB f64, vectors 20-41 MB"})
         line.update({
             "rel_err_b": err_b, "rel_err_dOmega_sampled": err_om,
-            "iters_forward": int(it_f.item()), "iters_adjoint": int(it_b.item()),
+            "iters_forward": iters_fb[0], "iters_adjoint": iters_fb[1],
+            "row_reduced": row_reduced,
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "traffic": None, "peak_source": src,
                          "algorithmic_bytes": kbytes[names[dom]], "ms": prof[dom]},
