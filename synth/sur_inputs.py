@@ -252,3 +252,25 @@ def config4(M: int = 40000, G: int = 128, nmin: int = 4, nmax: int = 24):
     Y, beta = draw_responses(g, X, L, M, 1)
     target = g.standard_normal((sum(n_i), 1))
     return SurProblem(X, L @ L.T, Y, beta, M, L, meta=dict(name=f"sur-grad-g{G}-m{M}")), L, target
+
+
+def monte_carlo_problem(count: int, seed: int = SEED_BASE + 77):
+    """The Monte-Carlo setup of the statistical study (Sec. 3.4): m = 80,
+    n = 20, Sigma with the four distinct eigenvalues 0.01, 0.1, 10, 50, read
+    as a SUR model G = 4, M = 20, n_i = 5, Omega = V diag(0.01, 0.1, 10, 50) V^T
+    (V Haar), so that each eigenvalue of Sigma = Omega (x) I_M has
+    multiplicity 20.  X iid N(0, 1) and beta fixed; `count` replications of
+    the disturbance as the columns of Y (G M x count).
+    Returns (X_blocks, Omega, beta (n, 1), Y, Xbeta (G M, 1))."""
+    g = rng(seed)
+    G, M = 4, 20
+    X = gaussian_blocks(g, M, [5, 5, 5, 5])
+    V = haar_orthogonal(g, G)
+    Omega = V @ np.diag([0.01, 0.1, 10.0, 50.0]) @ V.T
+    Omega = 0.5 * (Omega + Omega.T)
+    F = np.linalg.cholesky(Omega)
+    beta = g.standard_normal((20, 1))
+    Xb = np.vstack([X[i] @ beta[5 * i:5 * i + 5] for i in range(G)])
+    Z = g.standard_normal((G, M * count))
+    E = (F @ Z).reshape(G, M, count).reshape(G * M, count)   # rows of equation i: Z F^T, column by column
+    return X, Omega, beta, Xb + E, Xb
