@@ -82,7 +82,22 @@ typedef struct {
   int step_kernels;       /* GLM_SUR_STEP_*: kernels of the float32 bulk steps   */
   int precond;            /* GLM_SUR_PRECOND_*: the block D of the preconditioner
                              of eq. (invprec), D = D0 (x) I_M               */
+  int algorithm;          /* GLM_SUR_ALG_*: Algorithm glmpcg2 or glmpcg3      */
 } glm_sur_opts;
+
+enum {
+  GLM_SUR_ALG_GLMPCG2 = 0,  /* Algorithm glmpcg2 (default): u_{i+1} = Pi r_{i+1}
+                               + mu_i u_i, run in the reduced form of eq. (urwProj) */
+  GLM_SUR_ALG_GLMPCG3 = 1   /* Algorithm glmpcg3: the direction s_{i+1} = r_{i+1}
+                               + mu_i s_i is carried unprojected and u_i = Pi s_i
+                               is recomputed every step (two more passes over Q
+                               per step); w_{i+1} = w_i - lambda_i u_i, r_{i+1} =
+                               r_i - lambda_i (Sigma u_i + X X*^T s_i) with
+                               X X*^T s = s - Pi s.  Float64 only, no
+                               restrictions (GLM_SUR_INVALID_ARG otherwise); a
+                               column stops at tol, on breakdown or at maxit
+                               (no stagnation window).                     */
+};
 
 enum {
   GLM_SUR_PRECOND_IDENTITY = 0,  /* D = I (Sec. 4.3)                             */
@@ -110,6 +125,7 @@ enum {
 
 /* Default options: FP64, tol 1e-13, maxit m-n+1, W = 25, inner_tol 1e-5,
  * max_refine 8, chunk 16, inner_shift 0, reduce_rows 0, step_kernels AUTO,
+ * algorithm GLMPCG2,
  * precond IDENTITY.  A column that stops without
  * converging (stagnation, breakdown, maxit) returns its best saved iterate:
  * w is saved whenever c falls below a quarter of the c of the previous save. */

@@ -37,12 +37,16 @@ GLM_SUR_PRECOND_IDENTITY = 0
 GLM_SUR_PRECOND_SCALED = 1
 GLM_SUR_PRECOND_DIAG = 2
 
+GLM_SUR_ALG_GLMPCG2 = 0
+GLM_SUR_ALG_GLMPCG3 = 1
+
 
 class GlmSurOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("stagnation_window", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("chunk", ctypes.c_int), ("inner_shift", ctypes.c_double),
-                ("reduce_rows", ctypes.c_int), ("step_kernels", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("reduce_rows", ctypes.c_int), ("step_kernels", ctypes.c_int), ("precond", ctypes.c_int),
+                ("algorithm", ctypes.c_int)]
 
 
 # (name, restype, argtypes) of every exported entry point

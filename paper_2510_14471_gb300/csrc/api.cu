@@ -20,6 +20,7 @@
 #include "ne.h"
 #include "noalloc.h"
 #include "pcg.h"
+#include "pcg3.h"
 #include "reduce.h"
 #include "rglm.h"
 
@@ -131,6 +132,11 @@ struct glm_sur_ctx {
   double* ne_om = nullptr;     // Omega^-1 (G x Gq), then the Cholesky factor and its inverse (G x G each)
   int* ne_hact = nullptr;      // pinned copy of the active flags
   int necap = 0;
+  // Algorithm glmpcg3 (opts.algorithm): per-column state and d partials
+  double* p3_buf = nullptr;
+  int* p3_ibuf = nullptr;
+  int* p3_hact = nullptr;      // pinned copy of the active flags
+  int p3cap = 0;
   // restricted multivariate GLM (glm_sur_mvrglm_setup): the solves run on
   // `sub`, the G equations [R0; C_i] (N + kmax rows each) with Sigma = 0 on
   // the restriction rows
@@ -159,6 +165,7 @@ glm_sur_status validate_opts(const glm_sur_opts* o) {
   if (!(o->inner_shift >= 0.0) || o->inner_shift > 1e-2) return GLM_SUR_INVALID_ARG;
   if (o->step_kernels != GLM_SUR_STEP_AUTO && o->step_kernels != GLM_SUR_STEP_SIMT) return GLM_SUR_INVALID_ARG;
   if (o->precond < GLM_SUR_PRECOND_IDENTITY || o->precond > GLM_SUR_PRECOND_DIAG) return GLM_SUR_INVALID_ARG;
+  if (o->algorithm != GLM_SUR_ALG_GLMPCG2 && o->algorithm != GLM_SUR_ALG_GLMPCG3) return GLM_SUR_INVALID_ARG;
   return GLM_SUR_OK;
 }
 
@@ -752,6 +759,7 @@ void glm_sur_default_opts(glm_sur_opts* o) {
   o->reduce_rows = 0;
   o->step_kernels = GLM_SUR_STEP_AUTO;
   o->precond = GLM_SUR_PRECOND_IDENTITY;
+  o->algorithm = GLM_SUR_ALG_GLMPCG2;
 }
 
 const char* glm_sur_status_string(glm_sur_status s) {
@@ -1216,6 +1224,86 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
 glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const double* d, int64_t ldd, int k, double* b,
                           int64_t ldb, int* iters, double* relres, cudaStream_t s);
 
+// Algorithm glmpcg3 in float64 on the right-hand sides in y64 (D = I on the
+// model of the handle: a preconditioner block acts through the row scaling).
+// Per step: u = P s (two passes over Q), S = Sigma u with d = u^T S, w and r,
+// g = P r with c' = g^T g (two passes over Q), s = r + mu s.
+glm_sur_status pcg3_core(glm_sur_t h, const IterPlan& p64, int k, double* b, int64_t ldb, int* iters, double* relres,
+                         cudaStream_t s) {
+  const Geom& gm = h->gm;
+  const int64_t m = gm.M * gm.G, mk = m * k;
+  const int nblk = 2 * h->sms;
+  if (k > h->p3cap) {
+    dfree(h->p3_buf);
+    dfree(h->p3_ibuf);
+    if (h->p3_hact) cudaFreeHost(h->p3_hact);
+    h->p3_hact = nullptr;
+    h->p3cap = 0;
+    GS_CUDA_TRY(dalloc(&h->p3_buf, (size_t)k * (5 + nblk)));
+    GS_CUDA_TRY(dalloc(&h->p3_ibuf, (size_t)3 * k));
+    GS_CUDA_TRY(cudaMallocHost(&h->p3_hact, kMaxRhs * sizeof(int)));
+    h->p3cap = k;
+  }
+  Pcg3State st;
+  st.k = k;
+  st.tol = h->opts.tol;
+  st.maxit = h->opts.maxit > 0 ? h->opts.maxit : (int)std::min<int64_t>(m - gm.n + 1, 1 << 30);
+  st.c = h->p3_buf;
+  st.c1 = st.c + k;
+  st.lam = st.c1 + k;
+  st.mu = st.lam + k;
+  st.relres = st.mu + k;
+  st.dpart = st.relres + k;
+  st.nblk = nblk;
+  st.active = h->p3_ibuf;
+  st.iters = st.active + k;
+  st.status = st.iters + k;
+  double *sv = h->wb64, *r = h->E64, *u = h->u64, *Sm = h->S64, *gP = h->g64, *w = h->w64;
+  double* Cpart = reinterpret_cast<double*>(h->Cpart);
+  const int ncp = p64.n_cpart;
+  GS_CUDA_TRY(cudaMemsetAsync(h->st.err, 0, sizeof(int), s));
+  GS_CUDA_TRY(cudaMemsetAsync(w, 0, mk * sizeof(double), s));
+  launch_pcg3_neg(mk, h->y64, r, s);                                   // r_1 = -y
+  auto project = [&](const double* x, double* px) {                    // px = P x; cpart: partials of px^T px
+    launch_proj_partial<double>(p64, gm, k, h->Q64, x, Cpart, h->st, 0, s);
+    launch_reduce<double>(p64, gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+    launch_proj_update<double>(p64, gm, k, h->Q64, x, px, h->C64, 0, nullptr, -1.0, h->cpart, h->st, 0, s);
+  };
+  project(r, gP);
+  launch_pcg3_after(st, h->cpart, ncp, 1, s);                          // c_1 = r^T Pi r
+  launch_pcg3_s(mk, k, st, r, sv, 1, s);                               // s_1 = r_1
+  h->launches += 6;
+  GS_CUDA_TRY(cudaGetLastError());
+  const int chunk = std::max(1, h->opts.chunk);
+  for (int it = 0; it < st.maxit;) {
+    const int steps = std::min(chunk, st.maxit - it);
+    for (int c = 0; c < steps; ++c) {
+      project(sv, u);                                                  // u = Pi s
+      launch_sigma_resid<double>(p64, gm, k, h->Om64, nullptr, u, Sm, s);   // Sm = -Sigma u
+      launch_pcg3_dot(gm.M, gm.G, k, u, Sm, st, s);
+      launch_pcg3_lambda(st, s);                                       // lambda = c / (u^T Sigma u)
+      launch_pcg3_wr(mk, k, st, u, Sm, sv, w, r, s);                   // w, r
+      project(r, gP);
+      launch_pcg3_after(st, h->cpart, ncp, 0, s);                      // c' = r^T Pi r, stop tests, mu
+      launch_pcg3_s(mk, k, st, r, sv, 0, s);                           // s = r + mu s
+    }
+    h->launches += 12 * steps;
+    GS_CUDA_TRY(cudaGetLastError());
+    it += steps;
+    GS_CUDA_TRY(cudaMemcpyAsync(h->p3_hact, st.active, k * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA_TRY(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < k; ++j) any |= h->p3_hact[j] != 0;
+    if (!any) break;
+  }
+  GS_CUDA_TRY(cudaMemcpyAsync(h->d_status_final, st.status, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  GS_CUDA_TRY(cudaMemcpyAsync(h->d_iters_acc, st.iters, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, st.iters, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (relres) GS_CUDA_TRY(cudaMemcpyAsync(relres, st.relres, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  h->last_k = k;
+  return recover_b(h, k, p64, b, ldb, s);
+}
+
 // MVRGLM solve: Y0 = Q0^T Y (model reduction), y' = [Y0_i; gamma_i; 0] per
 // equation, then the SUR iteration of the masked model; b = vec(B).
 glm_sur_status mv_solve(glm_sur_t h, const double* Y, int64_t ldy, const double* gamma, int64_t ldd, int k,
@@ -1268,6 +1356,8 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
   if (k < 1 || k > kMaxRhs || ldy < m || ldb < gm.n) return GLM_SUR_INVALID_ARG;
   if (h->kc > 0 && (h->opts.precision != GLM_SUR_PREC_FP64 || (d && ldd < h->kc))) return GLM_SUR_INVALID_ARG;
   if (h->kc > 0 && h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;
+  const bool pcg3 = h->opts.algorithm == GLM_SUR_ALG_GLMPCG3;
+  if (pcg3 && (h->kc > 0 || h->opts.precision != GLM_SUR_PREC_FP64)) return GLM_SUR_INVALID_ARG;
   IterPlan p64;
   glm_sur_status rc = prepare_solve(h, k, p64);
   if (rc != GLM_SUR_OK) return rc;
@@ -1277,7 +1367,7 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
   launch_colmajor_to_layout<double>(gm, k, Y, ldy, h->y64, 1.0, s, h->opts.precond ? h->d_isqrtd : nullptr);
   h->launches += 1;
   GS_CUDA_TRY(cudaGetLastError());
-  rc = solve_core(h, p64, d, ldd, k, b, ldb, iters, relres, s);
+  rc = pcg3 ? pcg3_core(h, p64, k, b, ldb, iters, relres, s) : solve_core(h, p64, d, ldd, k, b, ldb, iters, relres, s);
   if (rc != GLM_SUR_OK) return rc;
   h->has_w = true;
   h->w_restricted = h->kc > 0;
@@ -1703,6 +1793,8 @@ void glm_sur_destroy(glm_sur_t h) {
   dfree(h->Cmat); dfree(h->Nmat); dfree(h->Minv); dfree(h->cbuf); dfree(h->fbuf); dfree(h->gC);
   dfree(h->wfwd); dfree(h->lam1); dfree(h->opart);
   dfree(h->ne_buf); dfree(h->ne_ibuf); dfree(h->ne_om);
+  dfree(h->p3_buf); dfree(h->p3_ibuf);
+  if (h->p3_hact) cudaFreeHost(h->p3_hact);
   if (h->ne_hact) cudaFreeHost(h->ne_hact);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_norms) cudaFreeHost(h->h_norms);

@@ -151,7 +151,7 @@ k_sigma_step(int64_t M, int64_t Ms, int G, int Gq, int k, int TR, const T* __res
 
 // ---------------------------------------------------------------------------
 // sigma_resid: E = Y - W Omega on rows t < Ms, E = Y on the rows t >= Ms
-// (Sigma = 0 there); no state; used for b = X*^T (y - Sigma w)
+// (Sigma = 0 there), Y = 0 when null; no state; used for b = X*^T (y - Sigma w)
 // ---------------------------------------------------------------------------
 template <typename T, int JJ>
 __global__ void __launch_bounds__(256)
@@ -193,7 +193,7 @@ k_sigma_resid(int64_t M, int64_t Ms, int G, int Gq, int k, int TR, const T* __re
         const int h = 4 * hq + c;
         if (h < G) {
           const int64_t gi = ((t0 + t) * G + h) * k + jg * JJ + jj_t;
-          E[gi] = Y[gi] - acc[c];
+          E[gi] = (Y ? Y[gi] : (T)0) - acc[c];
         }
       }
     }

@@ -10,6 +10,7 @@ from . import _lib as L
 
 PRECISIONS = {"fp64": L.GLM_SUR_PREC_FP64, "fp32_refine": L.GLM_SUR_PREC_FP32_REFINE}
 STEP_KERNELS = {"auto": L.GLM_SUR_STEP_AUTO, "simt": L.GLM_SUR_STEP_SIMT}
+ALGORITHMS = {"glmpcg2": L.GLM_SUR_ALG_GLMPCG2, "glmpcg3": L.GLM_SUR_ALG_GLMPCG3}
 PRECONDS = {"identity": L.GLM_SUR_PRECOND_IDENTITY, "scaled": L.GLM_SUR_PRECOND_SCALED,
             "diag": L.GLM_SUR_PRECOND_DIAG}
 
@@ -35,7 +36,8 @@ class GlmSur:
     def __init__(self, X_blocks, Omega, precision: str = "fp64", tol: float = 1e-13, maxit: int = 0,
                  stagnation_window: int = 25, inner_tol: float = 1e-5, max_refine: int = 8,
                  chunk: int = 16, inner_shift: float = 0.0, reduce_rows: bool = False,
-                 step_kernels: str = "auto", precond: str = "identity", device="cuda"):
+                 step_kernels: str = "auto", precond: str = "identity", algorithm: str = "glmpcg2",
+                 device="cuda"):
         self.device = torch.device(device)
         blocks = [_dev_f64(x, self.device) for x in X_blocks]
         self.n_i = [int(x.shape[1]) for x in blocks]
@@ -57,6 +59,7 @@ class GlmSur:
         self.opts.reduce_rows = int(bool(reduce_rows))
         self.opts.step_kernels = STEP_KERNELS[step_kernels]
         self.opts.precond = PRECONDS[precond]
+        self.opts.algorithm = ALGORITHMS[algorithm]
         self.generation = 0     # number of solves so far (the adjoint belongs to the last one)
         self._h = L.glm_sur_setup(self.G, self.M, self.n_i, self._X.data_ptr(), self.M, self._Omega.data_ptr(),
                                   self.opts, self._stream())
