@@ -128,7 +128,7 @@ class ClockSampler:
 
 def make_problem(args):
     from synth import sur_inputs as S
-    return S.config1(k=args.k, M=args.M, G=args.G)
+    return S.singular_g64_m20000(k=args.k, M=args.M, G=args.G)
 
 
 def rel_err(b, ref):
@@ -147,10 +147,10 @@ def oracle_iteration_sample(p, n_iter):
 
 
 def oracle_iters_per_solve():
-    path = os.path.join(ROOT, "tests", "golden", "cfg1_oracle_iterations.json")
+    path = os.path.join(ROOT, "tests", "golden", "singular_g64_m20000_oracle_iterations.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return int(max(d["iters"])), "oracle float64 PCG to tol 1e-13 (tests/golden/cfg1_oracle_iterations.json)"
+        return int(max(d["iters"])), "oracle float64 PCG to tol 1e-13 (tests/golden/singular_g64_m20000_oracle_iterations.json)"
     return None, None
 
 
@@ -535,7 +535,7 @@ def run_batched(args, rank, world, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     k, count = 8, 2048
-    probs = S.config2_instances(count=count, k=k)
+    probs = S.batched_uneven_instances(count=count, k=k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     bt = GlmSurBatch([(q.X_blocks, q.Omega) for q in probs], device=dev)
@@ -670,7 +670,7 @@ def run_constrained(args, rank, world, local, pg):
     dev = torch.device("cuda", local)
     out = {}
     for k in (32, 1):
-        p = S.config3(k=k)
+        p = S.constrained_g32_m50000(k=k)
         h = GlmSur(p.X_blocks, p.Omega, precision="fp64", tol=1e-13, device=dev)
         h.set_restrictions(p.C)
         m, n, kc = p.m, p.n, p.C.shape[0]
@@ -749,7 +749,7 @@ def run_constrained(args, rank, world, local, pg):
         hr.close()
     cpu = None
     if rank == 0 and not args.no_cpu:
-        q = S.config3(k=k)
+        q = S.constrained_g32_m50000(k=k)
         n_it = 3
         t0 = time.perf_counter()
         O.rglm_pcg_aug(q.X_blocks, q.Omega, q.Y, q.C, q.d, tol=0.0, maxit=n_it, stag_window=10 ** 9)
@@ -799,7 +799,7 @@ def run_differentiable(args, rank, world, local, pg):
     from oracle import sur_oracle as O
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p, Lfac, target = S.config4()
+    p, Lfac, target = S.differentiable_g128_m40000()
     m, n, G, M = p.m, p.n, p.G, p.M
     h = GlmSur(p.X_blocks, p.Omega, precision="fp32_refine", stagnation_window=1000, max_refine=20, device=dev)
     Ycm = torch.as_tensor(p.Y.T.copy(), device=dev)
@@ -824,7 +824,7 @@ def run_differentiable(args, rank, world, local, pg):
     launches = (L.glm_sur_launch_count(h.handle) - l0) // (args.steps + args.warmup)
     ms, value = aggregate(ms, pg, world, dev)
     iters_fb = (int(it_f.item()), int(it_b.item()))
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "cfg4_reference.json")))
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "differentiable_g128_m40000_reference.json")))
     bb = b[0].cpu().numpy()
     err_b = float(np.linalg.norm(bb - np.asarray(gold["b"])) / np.linalg.norm(gold["b"]))
     om = dO.cpu().numpy().reshape(-1)[gold["dOmega_idx"]]

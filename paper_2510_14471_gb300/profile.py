@@ -49,7 +49,7 @@ def main(argv=None):
     from paper_2510_14471_gb300 import _lib as L
     from paper_2510_14471_gb300.sur import GlmSur
 
-    p = S.config1(k=a.k, M=a.M, G=a.G, rank=min(a.rank, a.G), nmin=a.nmin, nmax=a.nmax)
+    p = S.singular_g64_m20000(k=a.k, M=a.M, G=a.G, rank=min(a.rank, a.G), nmin=a.nmin, nmax=a.nmax)
     h = GlmSur(p.X_blocks, p.Omega, precision=a.precision, maxit=2, max_refine=1, step_kernels=a.step_kernels)
     h.solve(p.Y)
     torch.cuda.synchronize()
@@ -80,7 +80,7 @@ def profile_batch(a):
     from paper_2510_14471_gb300.sur import GlmSurBatch
 
     k = a.k if a.k in (1, 2, 4, 8) else 8   # batched solves take k in {1, 2, 4, 8}
-    probs = S.config2_instances(count=a.batch, k=k, Mmax=a.Mmax)
+    probs = S.batched_uneven_instances(count=a.batch, k=k, Mmax=a.Mmax)
     bt = GlmSurBatch([(q.X_blocks, q.Omega) for q in probs])
     Y = bt.pack_y([q.Y for q in probs])
     count = len(probs)

@@ -184,7 +184,7 @@ def haar_orthogonal(g: np.random.Generator, G: int):
 # the five named workloads
 # ----------------------------------------------------------------------------
 
-def config0(seed_offset: int = 0) -> SurProblem:
+def small_g3_m200(seed_offset: int = 0) -> SurProblem:
     """Plain SUR, FP64, one RHS: G=3, M=200, n_i=(5,4,6), Omega = L L^T."""
     g = rng(SEED_BASE + 0 + 1000 * seed_offset)
     X = gaussian_blocks(g, 200, [5, 4, 6])
@@ -193,7 +193,7 @@ def config0(seed_offset: int = 0) -> SurProblem:
     return SurProblem(X, L @ L.T, Y, beta, 200, L, meta=dict(name="sur-g3-m200"))
 
 
-def config1(k: int = 1, M: int = 20000, G: int = 64, rank: int = 56,
+def singular_g64_m20000(k: int = 1, M: int = 20000, G: int = 64, rank: int = 56,
             nmin: int = 8, nmax: int = 32) -> SurProblem:
     """Singular covariance: G=64, M=20000, n_i ~ U{8..32}, cond(X_i) <= 1e3,
     Omega = A A^T with A 64 x 56 (rank 56)."""
@@ -207,7 +207,7 @@ def config1(k: int = 1, M: int = 20000, G: int = 64, rank: int = 56,
                       meta=dict(name=f"sur-singular-g{G}-m{M}-k{k}"))
 
 
-def config2_instances(count: int = 2048, k: int = 8, Gmin: int = 2, Gmax: int = 12,
+def batched_uneven_instances(count: int = 2048, k: int = 8, Gmin: int = 2, Gmax: int = 12,
                       Mmin: int = 200, Mmax: int = 4000, nmin: int = 2, nmax: int = 10,
                       first: int = 0):
     """Batched uneven SUR instances (list of SurProblem): G ~ U{2..12},
@@ -228,7 +228,7 @@ def config2_instances(count: int = 2048, k: int = 8, Gmin: int = 2, Gmax: int = 
     return out
 
 
-def config3(k: int = 1, M: int = 50000, G: int = 32, ni: int = 16, kc: int = 64) -> SurProblem:
+def constrained_g32_m50000(k: int = 1, M: int = 50000, G: int = 32, ni: int = 16, kc: int = 64) -> SurProblem:
     """Constrained SUR: G=32, M=50000, n_i=16, C (64 x 512) iid N(0,1),
     d = C beta, Omega = V diag(lam) V^T, lam log-uniform [0.1, 10]."""
     g = rng(SEED_BASE + 3)
@@ -242,7 +242,7 @@ def config3(k: int = 1, M: int = 50000, G: int = 32, ni: int = 16, kc: int = 64)
                       meta=dict(name=f"sur-constrained-g{G}-m{M}-k{k}"))
 
 
-def config4(M: int = 40000, G: int = 128, nmin: int = 4, nmax: int = 24):
+def differentiable_g128_m40000(M: int = 40000, G: int = 128, nmin: int = 4, nmax: int = 24):
     """Differentiable SUR: G=128, M=40000, n_i ~ U{4..24}, Omega = L L^T,
     beta_target iid N(0,1).  Returns (problem, L, beta_target)."""
     g = rng(SEED_BASE + 4)

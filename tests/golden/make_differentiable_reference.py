@@ -1,4 +1,4 @@
-"""Writes cfg4_reference.json: reference values of the differentiable SUR
+"""Writes differentiable_g128_m40000_reference.json: reference values of the differentiable SUR
 workload G = 128, M = 40000, n_i ~ U{4..24}, Omega = L L^T (cond ~ 1e6),
 loss ||b - beta_target||^2, from the oracle's extended-precision iterative
 refinement (``sur_gls_refined``).  Stored: b in full, and dL/dy = lam and the
@@ -24,7 +24,7 @@ N_SAMPLE = 512
 
 if __name__ == "__main__":
     t0 = time.time()
-    p, Lfac, target = S.config4()
+    p, Lfac, target = S.differentiable_g128_m40000()
     fwd = O.sur_gls_refined(p.X_blocks, p.Omega, p.Y, steps=3)
     b = fwd["b"]
     gb = 2 * (b - target)
@@ -43,6 +43,6 @@ if __name__ == "__main__":
                dOmega_sym_norm=float(np.linalg.norm(gOs)), dOmega_idx=[int(i) for i in om_idx],
                dOmega_sym=[float(gOs.reshape(-1)[i]) for i in om_idx],
                seconds=time.time() - t0)
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "cfg4_reference.json"), "w") as f:
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "differentiable_g128_m40000_reference.json"), "w") as f:
         json.dump(out, f, indent=0)
     print({k: v for k, v in out.items() if not isinstance(v, list)}, out["corrections"])

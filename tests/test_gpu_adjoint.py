@@ -112,7 +112,7 @@ def _autograd_case(p, precision, target, Lfac):
 def test_autograd_cholesky_factor_vs_oracle_and_finite_differences():
     # Omega = L L^T parametrised by its lower factor; loss ||b - target||^2
     g = S.rng(80)
-    p, Lfac, target = S.config4(M=300, G=10, nmin=2, nmax=6)
+    p, Lfac, target = S.differentiable_g128_m40000(M=300, G=10, nmin=2, nmax=6)
     h, loss_of, Y, Lt = _autograd_case(p, "fp64", target, Lfac)
     gL = torch.tril(Lt.grad).cpu().numpy()
     gY = Y.grad.cpu().numpy()
@@ -160,7 +160,7 @@ CFG4_OPTS = dict(precision="fp32_refine", stagnation_window=1000, max_refine=20)
 
 
 def test_differentiable_workload_m2000_vs_refined_oracle():
-    p, Lfac, target = S.config4(M=2000)
+    p, Lfac, target = S.differentiable_g128_m40000(M=2000)
     ref = O.sur_gls_refined(p.X_blocks, p.Omega, p.Y, steps=3)
     gb = 2 * (ref["b"] - target)
     adj = O.sur_gls_refined(p.X_blocks, p.Omega, p.Y, gb, steps=3)
@@ -177,8 +177,8 @@ def test_differentiable_workload_m2000_vs_refined_oracle():
 def test_differentiable_workload_full_size_vs_reference_values():
     import json
     import os
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cfg4_reference.json")))
-    p, Lfac, target = S.config4()
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "differentiable_g128_m40000_reference.json")))
+    p, Lfac, target = S.differentiable_g128_m40000()
     assert (p.G, p.M, p.n) == (gold["G"], gold["M"], gold["n"])
     h = solver_for(p, **CFG4_OPTS)
     r = h.solve(p.Y)

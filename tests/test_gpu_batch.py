@@ -32,7 +32,7 @@ def run_batch(probs, k, reduce_rows=False):
 
 @pytest.mark.parametrize("k", [1, 4, 8])
 def test_small_batch_matches_oracle(k):
-    probs = S.config2_instances(count=24, k=k, Mmax=900)
+    probs = S.batched_uneven_instances(count=24, k=k, Mmax=900)
     bt, b, iters, relres, status = run_batch(probs, k)
     assert all(s in (0, 4) for s in status), status
     for j, p in enumerate(probs):
@@ -63,7 +63,7 @@ def test_batch_singular_and_edge_instances():
 def test_full_batch_workload_every_instance():
     # 2048 instances, G ~ U{2..12}, M ~ U{200..4000}, n_i ~ U{2..10}, k = 8:
     # every right-hand side of every instance against the structured oracle
-    probs = S.config2_instances(count=2048, k=8)
+    probs = S.batched_uneven_instances(count=2048, k=8)
     bt, b, iters, relres, status = run_batch(probs, 8)
     st = np.array(status).reshape(2048, 8)
     assert np.all(np.isin(st, (0, 4))), np.unique(st)
@@ -78,7 +78,7 @@ def test_full_batch_workload_every_instance():
 def test_row_reduced_batch_matches_oracle(k):
     # Remark rem:reduction per instance (M_j >= 2 n_j reduced to n_j rows,
     # the others kept whole): the estimates of the full models
-    probs = S.config2_instances(count=24, k=k, Mmax=900)
+    probs = S.batched_uneven_instances(count=24, k=k, Mmax=900)
     probs.append(S.make_problem(G=3, M=10, n_i=[4, 2, 3], k=k, seed=94, omega="chol"))   # M < 2n: kept whole
     bt, b, iters, relres, status = run_batch(probs, k, reduce_rows=True)
     assert all(s in (0, 4) for s in status), status
@@ -106,7 +106,7 @@ def test_row_reduced_batch_singular_omega_and_rank_deficient_fallback():
 def test_row_reduced_full_batch_workload_every_instance():
     # the 2048-instance workload on the reduced rows: every right-hand side
     # of every instance against the structured oracle
-    probs = S.config2_instances(count=2048, k=8)
+    probs = S.batched_uneven_instances(count=2048, k=8)
     bt, b, iters, relres, status = run_batch(probs, 8, reduce_rows=True)
     st = np.array(status).reshape(2048, 8)
     assert np.all(np.isin(st, (0, 4))), np.unique(st)

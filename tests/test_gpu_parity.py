@@ -77,7 +77,7 @@ def test_rank_deficient_block_is_reported():
 # ------------------------------------------------------------------ float64 PCG
 
 def test_config0_fp64_matches_dense_and_reference_pcg():
-    p = S.config0()
+    p = S.small_g3_m200()
     _, b_dense = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
     ref = O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=1e-13)
     r = gpu_solve(p, tol=1e-13)
@@ -165,7 +165,7 @@ def test_fp32_refine_matches_oracle(G, M, n_i, k, omega, rank):
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 def test_singular_omega_recovers_beta_true(precision):
     # Omega = A A^T of rank r < G with noise (A (x) I) z: b = beta_true exactly
-    p = S.config1(k=2, M=2000, G=16, rank=12)
+    p = S.singular_g64_m20000(k=2, M=2000, G=16, rank=12)
     r = gpu_solve(p, precision=precision, tol=1e-13)
     assert relcols(r["b"], p.beta) <= TOL_B
 
@@ -178,7 +178,7 @@ def test_full_size_singular_workload_recovers_beta_true(precision, k):
     # configuration the benchmark times, in its launch configuration.  With a
     # singular Omega the GLS estimate equals beta_true exactly, so every
     # output is checked without a full-size CPU solve.
-    p = S.config1(k=k)
+    p = S.singular_g64_m20000(k=k)
     r = gpu_solve(p, precision=precision)
     assert relcols(r["b"], p.beta) <= TOL_B, (r["status"], r["iters"])
 
@@ -221,7 +221,7 @@ def test_restricted_full_size_workload_every_column():
     # G = 32, M = 50000, n_i = 16, C 64 x 512, k = 32: the restrictions hold
     # for every column and every column matches the structured oracle (one
     # oracle call for all 32 right-hand sides: the QR of W is shared)
-    p = S.config3(k=32)
+    p = S.constrained_g32_m50000(k=32)
     r = gpu_solve_restricted(p)
     assert np.max(np.linalg.norm(p.C @ r["b"] - p.d, axis=0) / np.linalg.norm(p.d, axis=0)) <= 1e-10
     b_ref = O.sur_gls_structured(p.X_blocks, p.Omega, p.Y, p.C, p.d)

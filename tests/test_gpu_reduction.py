@@ -82,7 +82,7 @@ def test_reduced_adjoint_matches_oracle():
 
 def test_reduced_full_size_singular_workload():
     # the benchmark workload (M = 20000 rows reduced to n = 1234)
-    p = S.config1(k=16)
+    p = S.singular_g64_m20000(k=16)
     r = solver(p, precision="fp32_refine", reduce_rows=True).solve(p.Y)
     assert all(s in (0, 4) for s in r.status), r.status
     assert relcols(r.b.cpu().numpy(), p.beta) <= TOL

@@ -228,8 +228,8 @@ def test_scaling_experiment_condition_numbers_printed_in_paper():
         assert abs(ev.max() / ev.min() - expect) < 1e-6 * expect
 
 
-def test_pcg_matches_dense_on_config0():
-    p = S.config0()
+def test_pcg_matches_dense_on_the_small_workload():
+    p = S.small_g3_m200()
     _, b1 = O.aug_dense_solve(p.X_blocks, p.Omega, p.Y)
     b2 = O.gls_formula(p.X_blocks, p.Omega, p.Y)
     res = O.sur_pcg_aug(p.X_blocks, p.Omega, p.Y, tol=1e-13)
@@ -337,7 +337,7 @@ def test_refined_solution_matches_dense_and_converges():
     assert rel(out["lam"], lam_d) < 1e-11 and rel(out["dOmega"], gO_d) < 1e-11
     # an ill-conditioned Omega (G = 128, cond ~ 5e6): the first correction is
     # the normal equations' error, the later ones settle below 1e-15
-    q, Lf, _ = S.config4(M=20, G=128, nmin=2, nmax=4)
+    q, Lf, _ = S.differentiable_g128_m40000(M=20, G=128, nmin=2, nmax=4)
     assert np.linalg.cond(q.Omega) > 1e6
     out = O.sur_gls_refined(q.X_blocks, q.Omega, q.Y, steps=3)
     c = out["corrections"][0]

@@ -14,15 +14,15 @@ def test_generators_are_deterministic():
 
 
 def test_small_and_benchmark_workload_dimensions():
-    p = S.config0()
+    p = S.small_g3_m200()
     assert (p.G, p.M, p.n_i, p.k) == (3, 200, [5, 4, 6], 1)
-    q = S.config1(k=2, M=120)            # block widths do not depend on M
+    q = S.singular_g64_m20000(k=2, M=120)            # block widths do not depend on M
     assert q.G == 64 and q.n == 1234 and all(8 <= v <= 32 for v in q.n_i)
     assert np.linalg.matrix_rank(q.Omega) == 56   # Omega = A A^T, A 64 x 56
 
 
 def test_batched_instances_follow_their_ranges():
-    probs = S.config2_instances(count=16, k=8)
+    probs = S.batched_uneven_instances(count=16, k=8)
     for p in probs:
         assert 2 <= p.G <= 12 and 200 <= p.M <= 4000 and all(2 <= v <= 10 for v in p.n_i)
         assert abs(np.trace(p.Omega) - 1.0) < 1e-12 and p.Y.shape == (p.G * p.M, 8)
@@ -30,10 +30,10 @@ def test_batched_instances_follow_their_ranges():
 
 
 def test_constrained_and_differentiable_workloads():
-    c = S.config3(k=2, M=60)
+    c = S.constrained_g32_m50000(k=2, M=60)
     assert c.n == 512 and c.C.shape == (64, 512) and np.allclose(c.d, c.C @ c.beta)
     ev = np.linalg.eigvalsh(c.Omega)
     assert 0.099 < ev.min() and ev.max() < 10.01
-    d, L, target = S.config4(M=30)
+    d, L, target = S.differentiable_g128_m40000(M=30)
     assert d.G == 128 and d.n == 1793 and target.shape == (1793, 1)
     assert np.allclose(np.triu(L, 1), 0) and np.allclose(d.Omega, L @ L.T)
