@@ -853,8 +853,8 @@ def run_differentiable(args, rank, world, local, pg):
                          f"{dt:.1f} s"}
     # the same forward + adjoint on the row-reduced model (Remark
     # rem:reduction: 40000 rows per equation -> n; dL/dY = Q dL/dy')
-    hr = GlmSur(p.X_blocks, p.Omega, precision="fp32_refine", stagnation_window=1000, max_refine=20,
-                reduce_rows=True, device=dev)
+    # (float64 steps: the float32-refined solve of the reduced model stops near 1e-5)
+    hr = GlmSur(p.X_blocks, p.Omega, precision="fp64", stagnation_window=1000, reduce_rows=True, device=dev)
 
     def step_r():
         L.glm_sur_solve(hr.handle, Ycm.data_ptr(), m, 1, b.data_ptr(), n, it_f.data_ptr(), rr.data_ptr(), stream)
@@ -871,7 +871,9 @@ def run_differentiable(args, rank, world, local, pg):
                    "rel_err_dOmega_sampled": float(np.linalg.norm(omr - np.asarray(gold["dOmega_sym"])) /
                                                    np.linalg.norm(gold["dOmega_sym"])),
                    "iters_forward": int(it_f.item()), "iters_adjoint": int(it_b.item()),
-                   "note": f"every equation on its n = {n} rotated rows; float64 products Q^T y and Q dL/dy'"}
+                   "precision": "fp64",
+                   "note": f"every equation on its n = {n} rotated rows, float64 PCG steps; float64 products "
+                           f"Q^T y and Q dL/dy'"}
     hr.close()
     # end to end: Y from the host, b, dL/dY and dL/dOmega back
     Y2 = torch.empty_like(Ycm)
