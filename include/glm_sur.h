@@ -110,8 +110,12 @@ enum {
                                     sqrt(delta_a delta_b)); solves run that model
                                     and return the same b.  relres refers to it;
                                     a delta_i <= 0 is taken as 1.  Not with
-                                    restrictions, glm_sur_backward or
-                                    glm_sur_get_w (GLM_SUR_INVALID_ARG).        */
+                                    restrictions (GLM_SUR_INVALID_ARG).
+                                    glm_sur_get_w and glm_sur_backward map back
+                                    to the given model: w = S w~, dL/dy = S
+                                    dL/dy~, dL/dOmega = D0^-1/2 dL/dOmega~
+                                    D0^-1/2 (S = D0^-1/2 (x) I_M; b does not
+                                    depend on D0).                              */
 };
 
 enum {

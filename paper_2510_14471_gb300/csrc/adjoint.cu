@@ -22,12 +22,14 @@ namespace {
 constexpr int kOmTile = 32;     // output tile of the Omega gradient (32 x 32)
 constexpr int kOmPairs = 32;    // (row, rhs) pairs staged per pass
 
-// z_i = R_i^-T g_i (forward substitution, R_i row-major upper triangular),
-// written to the padded coefficient layout C[(poff_i + r) * k + j] with the
-// pad columns of block i set to zero.  One thread per (block, rhs).
+// z_i = s_i R_i^-T g_i (forward substitution, R_i row-major upper
+// triangular; s_i = blk_scale[i], or 1 when blk_scale is null), written to
+// the padded coefficient layout C[(poff_i + r) * k + j] with the pad columns
+// of block i set to zero.  One thread per (block, rhs).
 __global__ void k_adj_seed(int G, int k, const double* __restrict__ R, const int64_t* __restrict__ r_off,
                            const int* __restrict__ n_i, const int* __restrict__ off, const int* __restrict__ poff,
-                           const double* __restrict__ gb, int64_t ldg, double* __restrict__ C) {
+                           const double* __restrict__ gb, int64_t ldg, const double* __restrict__ blk_scale,
+                           double* __restrict__ C) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= G * k) return;
   const int i = id / k, j = id % k;
@@ -39,8 +41,9 @@ __global__ void k_adj_seed(int G, int k, const double* __restrict__ R, const int
     for (int c = 0; c < r; ++c) s -= Ri[c * ni + r] * z[c];
     z[r] = s / Ri[r * ni + r];
   }
+  const double sc = blk_scale ? blk_scale[i] : 1.0;
   const int w = poff[i + 1] - poff[i];
-  for (int r = 0; r < w; ++r) C[(int64_t)(poff[i] + r) * k + j] = r < ni ? z[r] : 0.0;
+  for (int r = 0; r < w; ++r) C[(int64_t)(poff[i] + r) * k + j] = r < ni ? sc * z[r] : 0.0;
 }
 
 // part[ch][a][b] = sum over the (t, j) pairs of chunk ch of Lam[t,a,j] W[t,b,j]
@@ -89,25 +92,26 @@ k_adj_omega_partial(int64_t M, int G, int k, int64_t chunk, const double* __rest
   }
 }
 
-// out[a + b * ldo] = -(1/2) sum_ch (part[ch][a][b] + part[ch][b][a])   (fixed order)
+// out[a + b * ldo] = -(1/2) s_a s_b sum_ch (part[ch][a][b] + part[ch][b][a])   (fixed order;
+// s = blk_scale, or 1 when it is null)
 __global__ void k_adj_omega_reduce(int G, int nch, const double* __restrict__ part, double* __restrict__ out,
-                                   int64_t ldo) {
+                                   int64_t ldo, const double* __restrict__ blk_scale) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)G * G) return;
   const int a = (int)(idx % G), b = (int)(idx / G);
   const int64_t GG = (int64_t)G * G;
   double s = 0.0;
   for (int ch = 0; ch < nch; ++ch) s += part[ch * GG + (int64_t)a * G + b] + part[ch * GG + (int64_t)b * G + a];
-  out[(int64_t)b * ldo + a] = -0.5 * s;
+  out[(int64_t)b * ldo + a] = blk_scale ? -0.5 * blk_scale[a] * blk_scale[b] * s : -0.5 * s;
 }
 
 }  // namespace
 
 void launch_adj_seed(const Geom& gm, int k, const double* R, const double* gb, int64_t ldg, double* C,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* blk_scale) {
   const int n = gm.G * k;
   k_adj_seed<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(gm.G, k, R, gm.d_r_off, gm.d_n_i, gm.d_off, gm.d_poff, gb,
-                                                       ldg, C);
+                                                       ldg, blk_scale, C);
 }
 
 int adj_omega_chunks(const Geom& gm, int k, int sms) {
@@ -120,13 +124,13 @@ int adj_omega_chunks(const Geom& gm, int k, int sms) {
 }
 
 void launch_adj_omega(const Geom& gm, int k, const double* Lam, const double* W, double* part, int nch,
-                      double* out, int64_t ldo, cudaStream_t s) {
+                      double* out, int64_t ldo, cudaStream_t s, const double* blk_scale) {
   const int64_t pairs = gm.M * k;
   const int64_t chunk = ceil_div(ceil_div(pairs, nch), kOmPairs) * kOmPairs;
   const unsigned tg = (unsigned)ceil_div(gm.G, kOmTile);
   k_adj_omega_partial<<<dim3(tg, tg, nch), 256, 0, s>>>(gm.M, gm.G, k, chunk, Lam, W, part);
   const int64_t gg = (int64_t)gm.G * gm.G;
-  k_adj_omega_reduce<<<(unsigned)ceil_div(gg, 256), 256, 0, s>>>(gm.G, nch, part, out, ldo);
+  k_adj_omega_reduce<<<(unsigned)ceil_div(gg, 256), 256, 0, s>>>(gm.G, nch, part, out, ldo, blk_scale);
 }
 
 }  // namespace glmsur

@@ -1539,7 +1539,6 @@ glm_sur_status glm_sur_solve_restricted(glm_sur_t h, const double* Y, int64_t ld
 glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, int k, double* dL_dY, int64_t ldy,
                                 double* dL_dOmega, int64_t ldo, int* iters, double* relres, glm_sur_stream_t stream) {
   if (!h || !dL_db || (!dL_dY && !dL_dOmega) || h->mv_N) return GLM_SUR_INVALID_ARG;
-  if (h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;
   if (h->sub) {
     // the adjoint of the reduced model; dL/dy = Q dL/dy' (the rows outside
     // range(W) have lam = 0) and dL/dOmega is the reduced model's
@@ -1568,8 +1567,14 @@ glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, i
   if (rc != GLM_SUR_OK) return rc;
   const int64_t mk = m * k;
   GS_CUDA_TRY(cudaMemcpyAsync(h->wfwd, h->w64, mk * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  // lam_1 = Q R^-T dL/db: block by block X_i^T lam_1 = R_i^T Q_i^T Q_i R_i^-T g_i = g_i
-  launch_adj_seed(gm, k, h->R, dL_db, ldg, h->C64, s);
+  // lam_1 = Q R^-T dL/db: block by block X_i^T lam_1 = R_i^T Q_i^T Q_i R_i^-T g_i = g_i.
+  // With a preconditioner block the iteration's model is the row-scaled one
+  // (X_i / sqrt(delta_i), Omega~ = D0^-1/2 Omega D0^-1/2, y~ = S y, S =
+  // D0^-1/2 (x) I_M), whose R_i^-T is sqrt(delta_i) R_i^-T.  b does not depend
+  // on D0, so dL/dy = S dL/dy~ and dL/dOmega = D0^-1/2 dL/dOmega~ D0^-1/2.
+  const double* sq = h->opts.precond != GLM_SUR_PRECOND_IDENTITY ? h->d_sqrtd : nullptr;
+  const double* isq = h->opts.precond != GLM_SUR_PRECOND_IDENTITY ? h->d_isqrtd : nullptr;
+  launch_adj_seed(gm, k, h->R, dL_db, ldg, h->C64, s, sq);
   GS_CUDA_TRY(cudaMemsetAsync(h->E64, 0, mk * sizeof(double), s));
   launch_proj_update<double>(p64, gm, k, h->Q64, h->E64, h->lam1, h->C64, 0, nullptr, 1.0, h->cpart, h->st, 0, s);
   // y' = 0 - Sigma lam_1; the remaining lam_2 solves eq. (aug1) for y'
@@ -1583,11 +1588,11 @@ glm_sur_status glm_sur_backward(glm_sur_t h, const double* dL_db, int64_t ldg, i
   launch_add_to_f64<double>(mk, h->lam1, h->w64, s);
   h->launches += 1;
   if (dL_dY) {
-    launch_layout_to_colmajor<double>(gm, k, h->w64, dL_dY, ldy, s);
+    launch_layout_to_colmajor<double>(gm, k, h->w64, dL_dY, ldy, s, isq);
     h->launches += 1;
   }
   if (dL_dOmega) {
-    launch_adj_omega(gm, k, h->w64, h->wfwd, h->opart, nch, dL_dOmega, ldo, s);
+    launch_adj_omega(gm, k, h->w64, h->wfwd, h->opart, nch, dL_dOmega, ldo, s, isq);
     h->launches += 2;
   }
   GS_CUDA_TRY(cudaMemcpyAsync(h->w64, h->wfwd, mk * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1644,9 +1649,10 @@ glm_sur_status glm_sur_get_status(glm_sur_t h, int* status, int k) {
 glm_sur_status glm_sur_get_w(glm_sur_t h, double* w, int64_t ldw, glm_sur_stream_t stream) {
   if (h && h->sub) return GLM_SUR_INVALID_ARG;   // w of the unreduced rows is not formed
   if (!h || !w || !h->has_w || ldw < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
-  if (h->opts.precond != GLM_SUR_PRECOND_IDENTITY) return GLM_SUR_INVALID_ARG;   // w of the row-scaled model
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  launch_layout_to_colmajor<double>(h->gm, h->last_k, h->w64, w, ldw, s);
+  // the row-scaled model's w~ solves it for S^-1 w: w = S w~, S = D0^-1/2 (x) I_M
+  launch_layout_to_colmajor<double>(h->gm, h->last_k, h->w64, w, ldw, s,
+                                    h->opts.precond != GLM_SUR_PRECOND_IDENTITY ? h->d_isqrtd : nullptr);
   GS_CUDA_TRY(cudaGetLastError());
   return GLM_SUR_OK;
 }

@@ -1179,7 +1179,7 @@ __global__ void k_colmajor_to_layout(int64_t M, int G, int k, const double* __re
 // Y[j*ldy + i*M + t] = in[(t*G + i)*k + j]
 template <typename Tin>
 __global__ void k_layout_to_colmajor(int64_t M, int G, int k, const Tin* __restrict__ in, double* __restrict__ Y,
-                                     int64_t ldy) {
+                                     int64_t ldy, const double* __restrict__ blk_scale) {
   __shared__ double tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32;
   const int64_t c0 = (int64_t)blockIdx.y * 32;
@@ -1194,7 +1194,7 @@ __global__ void k_layout_to_colmajor(int64_t M, int G, int k, const Tin* __restr
     const int64_t c = c0 + r, t = t0 + tx;
     if (c < ncol && t < M) {
       const int64_t i = c / k, j = c % k;
-      Y[j * ldy + i * M + t] = tile[tx][r];
+      Y[j * ldy + i * M + t] = blk_scale ? blk_scale[i] * tile[tx][r] : tile[tx][r];
     }
   }
 }
@@ -1495,9 +1495,10 @@ void launch_colmajor_to_layout(const Geom& gm, int k, const double* Y, int64_t l
   k_colmajor_to_layout<Tout><<<grid, 256, 0, s>>>(gm.M, gm.G, k, Y, ldy, out, scale, blk_scale);
 }
 template <typename Tin>
-void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s) {
+void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s,
+                               const double* blk_scale) {
   dim3 grid((unsigned)ceil_div(gm.M, 32), (unsigned)ceil_div((int64_t)gm.G * k, 32));
-  k_layout_to_colmajor<Tin><<<grid, 256, 0, s>>>(gm.M, gm.G, k, in, Y, ldy);
+  k_layout_to_colmajor<Tin><<<grid, 256, 0, s>>>(gm.M, gm.G, k, in, Y, ldy, blk_scale);
 }
 
 void launch_tri_solve(const Geom& gm, int k, const double* R, const double* C, double* b, int64_t ldb,
@@ -1595,7 +1596,8 @@ template void launch_proj_update<float>(const IterPlan&, const Geom&, int, const
                                         cudaStream_t);
 template void launch_colmajor_to_layout<double>(const Geom&, int, const double*, int64_t, double*, double,
                                                 cudaStream_t, const double*);
-template void launch_layout_to_colmajor<double>(const Geom&, int, const double*, double*, int64_t, cudaStream_t);
+template void launch_layout_to_colmajor<double>(const Geom&, int, const double*, double*, int64_t, cudaStream_t,
+                                                const double*);
 template void launch_convert<double, float>(int64_t, const double*, float*, double, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float*, double*, double, cudaStream_t);
 template void launch_colsumsq<double>(const IterPlan&, const Geom&, int, const double*, double*, cudaStream_t);

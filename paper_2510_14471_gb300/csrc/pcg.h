@@ -102,7 +102,8 @@ template <typename Tout>
 void launch_colmajor_to_layout(const Geom& gm, int k, const double* Y, int64_t ldy, Tout* out, double scale,
                                cudaStream_t s, const double* blk_scale = nullptr);
 template <typename Tin>
-void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s);
+void launch_layout_to_colmajor(const Geom& gm, int k, const Tin* in, double* Y, int64_t ldy, cudaStream_t s,
+                               const double* blk_scale = nullptr);
 void launch_tri_solve(const Geom& gm, int k, const double* R, const double* C, double* b, int64_t ldb,
                       cudaStream_t s, const double* blk_scale = nullptr);
 void launch_precond_omega(int G, int Gq, int kind, const double* Om, double* Om_out, double* sqrtd, double* isqrtd,

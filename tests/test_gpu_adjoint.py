@@ -199,3 +199,58 @@ def test_differentiable_workload_full_size_vs_reference_values():
     assert rel(om[gold["dOmega_idx"]], np.asarray(gold["dOmega_sym"])) <= TOL
     # adjoint identity X^T lam = dL/db
     assert rel(xt_lam(p, lam[:, None]), gb) <= TOL
+
+
+def test_differentiable_workload_full_size_reduced_diag_with_central_differences():
+    """The differentiable workload through the path its benchmark times: the
+    row-reduced model (Remark rem:reduction) with the preconditioner block D
+    = diag(Sigma), float64 steps.  b, dL/dy and dL/dOmega against the stored
+    reference values, then central differences (h = 1e-6) of the GPU loss
+    along 8 directions of Y and 8 of the Cholesky factor L of Omega = L L^T.
+    Two forward solves whose b is within TOL move a difference quotient by at
+    most 2 ||b - t|| ||b|| TOL / h; the loss is quadratic in Y and smooth in
+    L, so that bound (plus 1e-6 relative for truncation) is the tolerance."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "differentiable_g128_m40000_reference.json")))
+    p, Lfac, target = S.differentiable_g128_m40000()
+    h = solver_for(p, precision="fp64", precond="diag", stagnation_window=1000, reduce_rows=True)
+    r = h.solve(p.Y)
+    assert all(s == 0 for s in r.status), r.status
+    b = r.b.cpu().numpy()
+    assert rel(b, np.asarray(gold["b"])[:, None]) <= TOL
+    gb = 2 * (b - target)
+    dY, dO, iters, relres, status = h.backward(gb)
+    assert all(s == 0 for s in status), status
+    lam = dY.cpu().numpy()[:, 0]
+    gO = dO.cpu().numpy()
+    om = gO.reshape(-1)
+    assert abs(np.linalg.norm(lam) / gold["lam_norm"] - 1) <= TOL
+    assert rel(lam[gold["lam_idx"]], np.asarray(gold["lam"])) <= TOL
+    assert abs(np.linalg.norm(om) / gold["dOmega_sym_norm"] - 1) <= TOL
+    assert rel(om[gold["dOmega_idx"]], np.asarray(gold["dOmega_sym"])) <= TOL
+    gL = np.tril(2 * gO @ Lfac)                    # dL/dL for Omega = L L^T (gO symmetric)
+
+    def loss(Y):
+        bb = h.solve(Y).b.cpu().numpy()
+        return float(np.sum((bb - target) ** 2))
+
+    hstep = 1e-6
+    noise = 2 * np.linalg.norm(b - target) * np.linalg.norm(b) * TOL / hstep
+    g = S.rng(81)
+    for _ in range(8):
+        D = g.standard_normal(p.Y.shape)
+        fd = (loss(p.Y + hstep * D) - loss(p.Y - hstep * D)) / (2 * hstep)
+        an = float(np.sum(lam * D[:, 0]))
+        assert abs(fd - an) <= noise + 1e-6 * abs(an), (fd, an, noise)
+    for _ in range(8):
+        E = np.tril(g.standard_normal(Lfac.shape))
+        Lp, Lm = Lfac + hstep * E, Lfac - hstep * E
+        h.set_omega(Lp @ Lp.T)
+        lp = loss(p.Y)
+        h.set_omega(Lm @ Lm.T)
+        lm = loss(p.Y)
+        fd = (lp - lm) / (2 * hstep)
+        an = float(np.sum(gL * E))
+        assert abs(fd - an) <= noise + 1e-6 * abs(an), (fd, an, noise)
+    h.close()

@@ -86,10 +86,42 @@ def test_precond_refusals():
     from paper_2510_14471_gb300.sur import GlmSur
     p = S.make_problem(G=3, M=60, n_i=[3, 2, 3], k=1, seed=43, omega="chol", n_constraints=2)
     h = GlmSur(p.X_blocks, p.Omega, precision="fp64", precond="diag")
-    r = h.solve(p.Y)
-    with pytest.raises(L.GlmSurError):
-        h.backward(2 * r.b.cpu().numpy())
+    h.solve(p.Y)
     h.set_restrictions(p.C)
     with pytest.raises(L.GlmSurError):
         h.solve(p.Y, d=p.d)
+    h.close()
+
+
+@pytest.mark.parametrize("precond,precision,reduce_rows",
+                         [("diag", "fp64", False), ("scaled", "fp64", False), ("diag", "fp32_refine", False),
+                          ("diag", "fp64", True)])
+def test_precond_w_and_adjoint_match_oracle(precond, precision, reduce_rows):
+    """A preconditioner block changes the iteration's model, not b: get_w
+    returns the given model's w = S w~ and the adjoint its dL/dy = S dL/dy~
+    and dL/dOmega = D0^-1/2 dL/dOmega~ D0^-1/2, compared with the oracle's
+    Kronecker-inverse adjoint (eq. (GLS), Sigma^-1 = Omega^-1 (x) I_M) on an
+    Omega whose diagonal spans two decades."""
+    from paper_2510_14471_gb300.sur import GlmSur
+    n_i = [3, 7, 2, 9, 5, 4, 8, 6, 1, 10, 3, 5]
+    p = S.make_problem(G=12, M=700, n_i=n_i, k=2, seed=74, omega="chol")
+    dsc = np.logspace(-1.0, 1.0, p.G)
+    Om = p.Omega * np.sqrt(np.outer(dsc, dsc))
+    Y = p.Y.copy()
+    for i in range(p.G):
+        Y[i * p.M:(i + 1) * p.M] *= np.sqrt(dsc[i])
+    gb = S.rng(9).standard_normal((p.n, 2))
+    b_o, w_o, lam_o, gO = O.sur_gls_gradient_kron(p.X_blocks, Om, Y, gb)
+    h = GlmSur(p.X_blocks, Om, precision=precision, precond=precond, tol=1e-13, stagnation_window=1000,
+               reduce_rows=reduce_rows)
+    r = h.solve(Y)
+    assert relcols(r.b.cpu().numpy(), b_o) <= TOL_B
+    if not reduce_rows:                       # w of the rows outside range(W) is not formed on a reduced handle
+        assert relcols(h.w(2).cpu().numpy(), w_o) <= TOL_B
+    dY, dO, iters, relres, status = h.backward(gb)
+    assert all(s in (0, 4) for s in status), status
+    lam = dY.cpu().numpy()
+    assert relcols(lam, lam_o) <= TOL_B
+    gs = 0.5 * (gO + gO.T)
+    assert np.linalg.norm(dO.cpu().numpy() - gs) <= TOL_B * np.linalg.norm(gs)
     h.close()
