@@ -214,7 +214,7 @@ def run_extras(timeout_s=420):
         keep = ["value", "unit", "ms_per_step", "dtype", "config", "roofline", "roofline_iter", "e2e", "gpu_launches",
                 "clocks", "rel_err_sampled", "rel_err", "status_counts", "steps_per_instance", "iters_max", "k1",
                 "grad_err", "b_err", "steps", "models", "row_reduced", "full_model", "rel_err_b",
-                "rel_err_dOmega_sampled", "speedup_vs_full_model"]
+                "rel_err_dOmega_sampled", "speedup_vs_full_model", "balance"]
         out[w] = {k2: line[k2] for k2 in keep if k2 in line}
         out[w]["wall_s"] = time.perf_counter() - t0
     return out
@@ -515,6 +515,21 @@ def timed(fn, steps, warmup, local, pg):
     return ev0.elapsed_time(ev1) / steps, clk.summary()
 
 
+def batch_balance(L, handle, count, ms, clocks):
+    """Load balance of one persistent batch launch from the per-instance
+    cycle counts the kernel records (SM clock): the longest instance, and the
+    ideal time, the instances' total time spread evenly over the launch's
+    CTAs (all resident at once: SMs x CTAs per SM)."""
+    steps, cycles = L.glm_sur_batch_get_work(handle, count)
+    grid = L.glm_sur_batch_grid(handle)
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    inst_ms = np.asarray(cycles, dtype=float) / (mhz * 1e3)
+    ideal = float(inst_ms.sum()) / grid if grid > 0 else 0.0
+    return {"batch_ms": ms, "longest_instance_ms": float(inst_ms.max()), "ideal_ms": ideal,
+            "batch_over_ideal": ms / ideal if ideal > 0 else None, "ctas": grid, "sm_mhz_used": mhz,
+            "note": "ideal = sum of the instances' own times / CTAs of the launch; times from clock64 per instance"}
+
+
 def base_line(args, world, metric, workload, value, unit, ms, dtype, config):
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -558,6 +573,7 @@ def run_batched(args, rank, world, local, pg):
     ms, clocks = timed(solve, args.steps, args.warmup, local, pg)
     launches = (L.glm_sur_batch_launch_count(bt.handle) - l0) // (args.steps + args.warmup)
     status = np.array(L.glm_sur_batch_get_status(bt.handle, count * k))
+    balance = batch_balance(L, bt.handle, count, ms, clocks)
     it = iters.view(count, k).cpu().numpy()
     ms, value = aggregate(ms, pg, world, dev)
     value *= count                           # instances solved per second (all k right-hand sides each)
@@ -619,7 +635,8 @@ def run_batched(args, rank, world, local, pg):
 
     solve_r()
     torch.cuda.synchronize()
-    ms_r, _ = timed(solve_r, args.steps, args.warmup, local, pg)
+    ms_r, clocks_r = timed(solve_r, args.steps, args.warmup, local, pg)
+    balance_r = batch_balance(L, btr.handle, count, ms_r, clocks_r)
     status_r = np.array(L.glm_sur_batch_get_status(btr.handle, count * k))
     ms_r, value_r = aggregate(ms_r, pg, world, dev)
     bsr, errs_r = br.cpu().numpy(), {}
@@ -629,7 +646,7 @@ def run_batched(args, rank, world, local, pg):
     row_reduced = {"value": value_r * count, "unit": "instance solves/s", "ms": ms_r, "setup_ms": setup_r_ms,
                    "rel_err_sampled": errs_r,
                    "status_counts": {int(v): int(c) for v, c in zip(*np.unique(status_r, return_counts=True))},
-                   "steps_max": int(itr.view(count, k).max().item()),
+                   "steps_max": int(itr.view(count, k).max().item()), "balance": balance_r,
                    "note": "every instance with M >= 2n on its n rows; one float64 product Q_W^T Y per instance"}
     btr.close()
     if rank == 0:
@@ -641,7 +658,7 @@ def run_batched(args, rank, world, local, pg):
             "rel_err_sampled": errs, "status_counts": {int(v): int(c) for v, c in zip(*np.unique(status, return_counts=True))},
             "steps_per_instance": {"min": int(steps_j.min()), "median": float(np.median(steps_j)),
                                    "max": int(steps_j.max())},
-            "setup_ms": setup_ms,
+            "setup_ms": setup_ms, "balance": balance,
             "roofline": {"bound": "hbm", "kernel": "k_batch_solve", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "traffic": None, "peak_source": src, "algorithmic_bytes": alg,
                          "ms": ms, "note": "lower bound of the work: steps per instance = max over its columns"},

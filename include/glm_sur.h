@@ -437,6 +437,10 @@ glm_sur_status glm_sur_batch_get_work(glm_sur_batch_t h, int* steps, long long* 
  * (HOST, 3, nullable) receives the timed candidates (8, 16, 32 rows; 0 = not
  * timed: tuning stops once a candidate is 10% slower than the best). */
 int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms);
+/* CTAs of the persistent batch launch (SMs x CTAs resident per SM at the
+ * chosen tile height; 0 before the first solve, -1 for a NULL handle).
+ * Host-side query. */
+int glm_sur_batch_grid(glm_sur_batch_t h);
 int64_t glm_sur_batch_launch_count(glm_sur_batch_t h);
 void glm_sur_batch_destroy(glm_sur_batch_t h);
 

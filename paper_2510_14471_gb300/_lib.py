@@ -79,6 +79,7 @@ SIGNATURES = {
     "glm_sur_batch_get_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "glm_sur_batch_get_work": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
     "glm_sur_batch_tile": (_I, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "glm_sur_batch_grid": (_I, [_VP]),
     "glm_sur_batch_launch_count": (ctypes.c_int64, [_VP]),
     "glm_sur_batch_destroy": (None, [_VP]),
     "glm_sur_status_string": (ctypes.c_char_p, [_I]),
@@ -253,6 +254,10 @@ def glm_sur_batch_get_work(h: int, count: int):
     cycles = (ctypes.c_longlong * count)()
     check(lib().glm_sur_batch_get_work(h, steps, cycles), "glm_sur_batch_get_work")
     return [int(v) for v in steps], [int(v) for v in cycles]
+
+
+def glm_sur_batch_grid(h: int) -> int:
+    return int(lib().glm_sur_batch_grid(h))
 
 
 def glm_sur_batch_tile(h: int):

@@ -476,7 +476,7 @@ void enqueue_steps(glm_sur_ctx* h, int k, int n, cudaStream_t s) {
         // pass A (u, S = U Omega on the tensor cores, d and C partials), reduce, pass B
         launch_tc_pass_a(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, h->wb32, h->st, h->cpart,
                          p.n_cpart + p.extra_cpart, h->dpart, Cpart, s);
-        launch_reduce<float>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s);
+        launch_reduce<float>(p, h->gm, k, Cpart, C, h->st, 1, h->dpart, s, true);
         launch_tc_pass_b(p, h->gm, k, h->Om32, h->Q32, h->g32, h->u32, h->w32, C, h->st, h->cpart, s);
         continue;
       }
@@ -599,21 +599,27 @@ glm_sur_status project_correction(glm_sur_ctx* h, int k, const IterPlan& p64, cu
 
 // b = R^-1 Q^T (y - Sigma w64)   (Algorithm glmpcg2 step 10, Sec. 4.3);
 // restricted: b = N^-1 ([R_i^T Q_i^T (y - Sigma w)_i] + C^T d)  (eq. rglm1m)
+// c_fresh: C64 already holds Q^T (y - Sigma w64) for the current w64 (the
+// last float64 residual of the refinement, with no correction taken back
+// since), so only the triangular solve remains.
 glm_sur_status recover_b(glm_sur_ctx* h, int k, const IterPlan& p64, double* b, int64_t ldb, cudaStream_t s,
-                         const double* d = nullptr, int64_t ldd = 0) {
+                         const double* d = nullptr, int64_t ldd = 0, bool c_fresh = false) {
   double* Cpart = reinterpret_cast<double*>(h->Cpart);
-  launch_sigma_resid<double>(p64, h->gm, k, h->Om64, h->y64, h->w64, h->E64, s);
-  launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
-  launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+  if (!c_fresh || h->kc > 0) {
+    launch_sigma_resid<double>(p64, h->gm, k, h->Om64, h->y64, h->w64, h->E64, s);
+    launch_proj_partial<double>(p64, h->gm, k, h->Q64, h->E64, Cpart, h->st, 0, s);
+    launch_reduce<double>(p64, h->gm, k, Cpart, h->C64, h->st, 0, nullptr, s);
+    h->launches += 3;
+  }
   if (h->kc > 0) {
     GS_CUDA_TRY(rglm_coef(h->gm, k, h->C64, h->R, h->Minv, h->Cmat, h->kc, h->kc, d, ldd, 1.0, h->cbuf, h->fbuf, b,
                           ldb, s));
-    h->launches += 4;
+    h->launches += 1;
     return GLM_SUR_OK;
   }
   // (a row-scaled model has R_i / sqrt(delta_i): b_i = sqrt(delta_i) R_i^-1 Q_i^T (y' - Sigma' w')_i)
   launch_tri_solve(h->gm, k, h->R, h->C64, b, ldb, s, h->opts.precond ? h->d_sqrtd : nullptr);
-  h->launches += 4;
+  h->launches += 1;
   GS_CUDA_TRY(cudaGetLastError());
   return GLM_SUR_OK;
 }
@@ -1124,6 +1130,7 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
   const int maxit = h->opts.maxit > 0 ? h->opts.maxit : (int)std::min<int64_t>(m - gm.n + 1, 1 << 30);
   GS_CUDA_TRY(cudaMemsetAsync(h->st.err, 0, sizeof(int), s));
   h->last_k = k;
+  bool c_fresh = false;
   if (fp64) {
     rc = reset_state(h, k, h->opts.tol, maxit, h->opts.stagnation_window, s);
     if (rc != GLM_SUR_OK) return rc;
@@ -1146,6 +1153,7 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
     std::vector<double> rho0(k, 0.0), prev(k, 0.0), cur(k, 0.0), rr_out(k, 0.0);
     std::vector<int> fin(k, kStatusRunning), mask(2 * k, 0);
     for (int outer = 0;; ++outer) {
+      c_fresh = false;
       rc = true_residual(h, k, p64, s);
       if (rc != GLM_SUR_OK) return rc;
       launch_sum_partials_sqrt(p64.n_cpart, k, h->cpart, h->norms, s);
@@ -1184,7 +1192,10 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
       }
       // (the host vector `mask` must outlive the copy above)
       GS_CUDA_TRY(cudaStreamSynchronize(s));
-      if (all_done) break;
+      if (all_done) {
+        c_fresh = !any_revert && d == nullptr;   // C64 = Q^T (y - Sigma w64) of the final w64
+        break;
+      }
       // inner float32 PCG on P Sigma_e d = rho (live columns)
       rc = reset_state(h, k, h->opts.inner_tol, maxit, std::max(kInnerStagnation, h->opts.stagnation_window), s);
       if (rc != GLM_SUR_OK) return rc;
@@ -1215,7 +1226,7 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
   }
   if (iters) GS_CUDA_TRY(cudaMemcpyAsync(iters, h->d_iters_acc, k * sizeof(int), cudaMemcpyDeviceToDevice, s));
   if (b) {
-    rc = recover_b(h, k, p64, b, ldb, s, d, ldd);
+    rc = recover_b(h, k, p64, b, ldb, s, d, ldd, c_fresh);
     if (rc != GLM_SUR_OK) return rc;
   }
   return GLM_SUR_OK;

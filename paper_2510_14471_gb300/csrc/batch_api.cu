@@ -600,6 +600,12 @@ int glm_sur_batch_tile(glm_sur_batch_t h, float* tune_ms) {
   return h->tile;
 }
 
+int glm_sur_batch_grid(glm_sur_batch_t h) {
+  if (h && h->inner) return glm_sur_batch_grid(h->inner);
+  if (!h) return -1;
+  return h->tile ? h->grid : 0;
+}
+
 int64_t glm_sur_batch_launch_count(glm_sur_batch_t h) {
   if (!h) return -1;
   return h->launches + (h->inner ? glm_sur_batch_launch_count(h->inner) : 0);

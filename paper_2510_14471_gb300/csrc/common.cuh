@@ -31,6 +31,35 @@ constexpr int kStatusRunning = -1;
 constexpr double kRefineMinGain = 0.5;
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel launched with the programmatic-serialization attribute may start
+// before the kernel ahead of it in the stream has finished; it must call
+// griddep_wait() before its first access to anything that kernel writes: the
+// wait returns once the prerequisite grid has completed and its memory
+// operations are visible.  griddep_launch_dependents() lets the next kernel
+// start launching (its blocks are placed as resources free up).  Both are
+// no-ops for a kernel launched without the attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch of `kern` with the programmatic-serialization attribute (host).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -271,6 +271,8 @@ k_reduce(int64_t nidx, int nrb, const T* __restrict__ Cpart, T* __restrict__ C, 
          const double* __restrict__ dpart, int ndpart) {
   __shared__ double part[8][33];
   __shared__ int nact_s;
+  griddep_launch_dependents();
+  griddep_wait();
   const int k = st.k;
   if (scalar && blockIdx.x == gridDim.x - 1) {
     // scalar step for all k columns
@@ -1266,8 +1268,31 @@ __global__ void __launch_bounds__(256)
 k_init_inner(int64_t M, int Gk, int k, const double* __restrict__ rho, const int* __restrict__ live, T* g, T* u,
              T* w, double* __restrict__ cpart) {
   __shared__ double red[8 * kMaxRhs];
+  __shared__ double sq[256];
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
   const int64_t e0 = r0 * Gk, e1 = r1 * Gk;
+  if (blockDim.x == 256 && 256 % k == 0) {
+    // e0 is a multiple of k and so is the stride: thread t always meets
+    // column t % k, and sums its squares in the same pass
+    const int j = threadIdx.x % k;
+    const bool on = live == nullptr || live[j];
+    double acc = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 256) {
+      const T gv = on ? (T)(-rho[e]) : (T)0;
+      g[e] = gv;
+      u[e] = (T)0;
+      if (w) w[e] = (T)0;
+      acc += (double)gv * (double)gv;
+    }
+    sq[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < k) {
+      double t = 0.0;
+      for (int q = threadIdx.x; q < 256; q += k) t += sq[q];   // fixed order
+      cpart[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+    }
+    return;
+  }
   for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     g[e] = (live == nullptr || live[e % k]) ? (T)(-rho[e]) : (T)0;
     u[e] = (T)0;
@@ -1474,10 +1499,14 @@ void launch_proj_partial(const IterPlan& p, const Geom& gm, int k, const T* Q, c
 }
 template <typename T>
 void launch_reduce(const IterPlan& p, const Geom& gm, int k, const T* Cpart, T* C, const PcgState& st, int scalar,
-                   const double* dpart, cudaStream_t s) {
+                   const double* dpart, cudaStream_t s, bool pdl) {
   const int64_t nidx = (int64_t)gm.np * k;
   const int nblk = (int)ceil_div(nidx, 32) + (scalar ? 1 : 0);
-  k_reduce<T><<<nblk, 256, 0, s>>>(nidx, p.n_partial_rows, Cpart, C, st, scalar, dpart, p.n_sigma);
+  if (pdl)
+    launch_pdl(k_reduce<T>, dim3(nblk), dim3(256), 0, s, nidx, p.n_partial_rows, Cpart, C, st, scalar, dpart,
+               p.n_sigma);
+  else
+    k_reduce<T><<<nblk, 256, 0, s>>>(nidx, p.n_partial_rows, Cpart, C, st, scalar, dpart, p.n_sigma);
 }
 template <typename T>
 void launch_proj_update(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g, const T* C,
@@ -1585,9 +1614,9 @@ template void launch_proj_partial<double>(const IterPlan&, const Geom&, int, con
 template void launch_proj_partial<float>(const IterPlan&, const Geom&, int, const float*, const float*, float*,
                                          const PcgState&, int, cudaStream_t);
 template void launch_reduce<double>(const IterPlan&, const Geom&, int, const double*, double*, const PcgState&, int,
-                                    const double*, cudaStream_t);
+                                    const double*, cudaStream_t, bool);
 template void launch_reduce<float>(const IterPlan&, const Geom&, int, const float*, float*, const PcgState&, int,
-                                   const double*, cudaStream_t);
+                                   const double*, cudaStream_t, bool);
 template void launch_proj_update<double>(const IterPlan&, const Geom&, int, const double*, const double*, double*,
                                          const double*, int, const double*, double, double*, const PcgState&, int,
                                          cudaStream_t);

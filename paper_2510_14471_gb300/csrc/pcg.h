@@ -93,7 +93,7 @@ void launch_proj_partial(const IterPlan& p, const Geom& gm, int k, const T* Q, c
                          const PcgState& st, int use_state, cudaStream_t s);
 template <typename T>
 void launch_reduce(const IterPlan& p, const Geom& gm, int k, const T* Cpart, T* C, const PcgState& st, int scalar,
-                   const double* dpart, cudaStream_t s);
+                   const double* dpart, cudaStream_t s, bool pdl = false);
 template <typename T>
 void launch_proj_update(const IterPlan& p, const Geom& gm, int k, const T* Q, const T* S, T* g, const T* C,
                         int alpha, const double* lam, double lam_const, double* cpart, const PcgState& st,

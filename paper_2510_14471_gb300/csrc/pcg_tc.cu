@@ -169,6 +169,8 @@ k_tc_pass_a(int64_t M, int G, int Gq, int np, int nq, int TQ, int NSQ, const flo
   __shared__ int act_s[KK], snap_s[KK], anyp_s, abort_s;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  griddep_launch_dependents();
+  griddep_wait();        // the previous step's pass B, the reduce or the init kernels
   if (*st.err) return;   // an earlier bounded wait gave up: the run is being abandoned
   if (tid == 0) anyp_s = 0;
   const double csum = sum_partials<KK>(cpart, ncpart, KK, 0, red);
@@ -448,6 +450,8 @@ k_tc_pass_b(int64_t M, int G, int Gq, int np, int TQ, int NSQ, int NSG, const fl
   __shared__ int abort_s;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  griddep_launch_dependents();
+  griddep_wait();        // the reduce of this step (after pass A)
   if (*st.err) return;
   {
     const int slot = (*st.it - 1) & 1;   // reduce has already advanced the counter
@@ -733,20 +737,18 @@ cudaError_t tc_prepare(int k, int Gp, size_t a_bytes, size_t b_bytes) {
 void launch_tc_pass_a(const IterPlan& p, const Geom& gm, int k, const float* Om, const float* Q, const float* g,
                       float* u, const float* w, float* wbest, const PcgState& st, const double* cpart, int ncpart,
                       double* dpart, float* Cpart, cudaStream_t s) {
-#define A_(KK, HB)                                                                                                \
-  k_tc_pass_a<KK, HB><<<p.n_sigma, kTcThreads, p.tc_a_smem, s>>>(gm.M, gm.G, gm.Gq, gm.np, gm.nq, p.tc_tq_a,      \
-                                                                  p.tc_nsq_a, Om, Q, g, u, w, wbest, gm.d_quad_blk, \
-                                                                  st, cpart, ncpart, dpart, Cpart)
+#define A_(KK, HB)                                                                                          \
+  launch_pdl(k_tc_pass_a<KK, HB>, dim3(p.n_sigma), dim3(kTcThreads), p.tc_a_smem, s, gm.M, gm.G, gm.Gq, gm.np, \
+             gm.nq, p.tc_tq_a, p.tc_nsq_a, Om, Q, g, u, w, wbest, gm.d_quad_blk, st, cpart, ncpart, dpart, Cpart)
   TC_DISPATCH(k, p.tc_gp, A_);
 #undef A_
 }
 
 void launch_tc_pass_b(const IterPlan& p, const Geom& gm, int k, const float* Om, const float* Q, float* g,
                       const float* u, float* w, const float* C, const PcgState& st, double* cpart, cudaStream_t s) {
-#define B_(KK, HB)                                                                                                \
-  k_tc_pass_b<KK, HB><<<p.n_update, kTcThreads, p.tc_b_smem, s>>>(gm.M, gm.G, gm.Gq, gm.np, p.tc_tq_b, p.tc_nsq_b, \
-                                                                   p.tc_nsg, Om, Q, g, u, w, C, gm.d_poff, st,    \
-                                                                   cpart)
+#define B_(KK, HB)                                                                                          \
+  launch_pdl(k_tc_pass_b<KK, HB>, dim3(p.n_update), dim3(kTcThreads), p.tc_b_smem, s, gm.M, gm.G, gm.Gq, gm.np, \
+             p.tc_tq_b, p.tc_nsq_b, p.tc_nsg, Om, Q, g, u, w, C, gm.d_poff, st, cpart)
   TC_DISPATCH(k, p.tc_gp, B_);
 #undef B_
 }

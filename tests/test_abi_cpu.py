@@ -77,6 +77,7 @@ def test_host_only_calls(libpath):
     steps = (ctypes.c_int * 1)()
     assert L.glm_sur_batch_get_work(None, steps, None) == _lib.GLM_SUR_INVALID_ARG
     assert L.glm_sur_batch_tile(None, None) <= 0
+    assert L.glm_sur_batch_grid(None) == -1
 
 
 def test_product_package_does_not_import_the_oracle():
