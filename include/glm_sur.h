@@ -76,9 +76,13 @@ typedef struct {
                              rem:reduction (M' = n rows), when M >= 2 n,
                              n <= 2048 and W = [X_1 ... X_G] has full column
                              rank (otherwise the model is kept whole).  On a
-                             reduced handle tol, relres and the stop tests
-                             refer to the reduced system (responses Q^T y_i),
-                             not to the M-row model                          */
+                             reduced handle the residual is the reduced
+                             system's (responses Q^T y_i), and tol and relres
+                             are relative to the M-row model's ||P y||, whose
+                             square is the reduced ||P' y'||^2 plus the
+                             energy of y outside range(W) (taken as it is
+                             scaled by a preconditioner block).  The
+                             adjoint solve and PCG-NE need no such term    */
   int step_kernels;       /* GLM_SUR_STEP_*: kernels of the float32 bulk steps   */
   int precond;            /* GLM_SUR_PRECOND_*: the block D of the preconditioner
                              of eq. (invprec), D = D0 (x) I_M               */

@@ -120,6 +120,11 @@ struct glm_sur_ctx {
   double* Qw = nullptr;        // M x n column-major orthonormal basis of range(W)
   double* yred = nullptr;      // reduced responses / gradients, (G n) x k column-major
   int64_t yred_cap = 0;
+  // (on the reduced model) energy of the responses outside range(W), k
+  // values, added to the reference of relres and tol while c1x_on
+  double* c1x = nullptr;
+  double* c1x_part = nullptr;  // G x kMaxRhs workspace
+  bool c1x_on = false;
   // adjoint (glm_sur_backward)
   double* wfwd = nullptr;      // the forward w while the adjoint solve runs
   double* lam1 = nullptr;      // particular solution lam_1 = Q R^-T dL/db
@@ -435,6 +440,7 @@ glm_sur_status reset_state(glm_sur_ctx* h, int k, double tol, int maxit, int W, 
   st.tol = tol;
   st.maxit = maxit;
   st.W = W;
+  st.c1_extra = nullptr;
   GS_CUDA_TRY(cudaMemsetAsync(h->st_buf, 0, sizeof(double) * (size_t)kStateDoubles * h->kcap, s));
   GS_CUDA_TRY(cudaMemsetAsync(h->st_ibuf, 0, sizeof(int) * ((size_t)kStateInts * h->kcap + 2), s));
   // (the error word after them is cleared per solve, not per inner run)
@@ -1134,6 +1140,7 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
   if (fp64) {
     rc = reset_state(h, k, h->opts.tol, maxit, h->opts.stagnation_window, s);
     if (rc != GLM_SUR_OK) return rc;
+    h->st.c1_extra = h->c1x_on ? h->c1x : nullptr;
     rc = pcg_init<double>(h, k, h->y64, s, d, ldd);
     if (rc != GLM_SUR_OK) return rc;
     GS_CUDA_TRY(cudaGetLastError());
@@ -1150,8 +1157,10 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
     // residual has reached its float64 rounding floor.
     GS_CUDA_TRY(cudaMemsetAsync(h->w64, 0, mk * sizeof(double), s));
     GS_CUDA_TRY(cudaMemsetAsync(h->d_iters_acc, 0, k * sizeof(int), s));
-    std::vector<double> rho0(k, 0.0), prev(k, 0.0), cur(k, 0.0), rr_out(k, 0.0);
+    std::vector<double> rho0(k, 0.0), prev(k, 0.0), cur(k, 0.0), rr_out(k, 0.0), extra(k, 0.0);
     std::vector<int> fin(k, kStatusRunning), mask(2 * k, 0);
+    if (h->c1x_on)   // (read after the first synchronisation below)
+      GS_CUDA_TRY(cudaMemcpyAsync(extra.data(), h->c1x, k * sizeof(double), cudaMemcpyDeviceToHost, s));
     for (int outer = 0;; ++outer) {
       c_fresh = false;
       rc = true_residual(h, k, p64, s);
@@ -1163,7 +1172,7 @@ glm_sur_status solve_core(glm_sur_t h, const IterPlan& p64, const double* d, int
       bool all_done = true, any_revert = false;
       for (int j = 0; j < k; ++j) {
         cur[j] = h->h_norms[j];
-        if (outer == 0) rho0[j] = cur[j];
+        if (outer == 0) rho0[j] = std::sqrt(cur[j] * cur[j] + extra[j]);
         mask[k + j] = 0;
         if (fin[j] == kStatusRunning) {
           const double rr = rho0[j] > 0 ? cur[j] / rho0[j] : 0.0;
@@ -1266,6 +1275,7 @@ glm_sur_status pcg3_core(glm_sur_t h, const IterPlan& p64, int k, double* b, int
   st.relres = st.mu + k;
   st.dpart = st.relres + k;
   st.nblk = nblk;
+  st.c1_extra = h->c1x_on ? h->c1x : nullptr;
   st.active = h->p3_ibuf;
   st.iters = st.active + k;
   st.status = st.iters + k;
@@ -1360,7 +1370,24 @@ glm_sur_status solve_impl(glm_sur_t h, const double* Y, int64_t ldy, const doubl
     if (k < 1 || k > kMaxRhs || ldy < h->gm.M * h->gm.G) return GLM_SUR_INVALID_ARG;
     glm_sur_status rc = rotate_in(h, Y, ldy, k, s);
     if (rc != GLM_SUR_OK) return rc;
-    return solve_impl(h->sub, h->yred, (int64_t)h->gm.G * h->gm.n, d, ldd, k, b, ldb, iters, relres, s);
+    // tol and relres refer to the M-row model's ||P y||: its square is the
+    // reduced model's plus the energy of y outside range(W), where the
+    // model has no regressor and no restriction (scaled by D0^-1 under a
+    // preconditioner block, as the iteration sees it)
+    glm_sur_ctx* sb = h->sub;
+    if (!sb->c1x) {
+      GS_CUDA_TRY(dalloc(&sb->c1x, (size_t)kMaxRhs));
+      GS_CUDA_TRY(dalloc(&sb->c1x_part, (size_t)h->gm.G * kMaxRhs));
+    }
+    launch_complement_energy(h->gm.G, h->gm.M, h->gm.n, k, Y, ldy, h->yred,
+                             sb->opts.precond != GLM_SUR_PRECOND_IDENTITY ? sb->d_isqrtd : nullptr, sb->c1x_part,
+                             sb->c1x, s);
+    h->launches += 2;
+    GS_CUDA_TRY(cudaGetLastError());
+    sb->c1x_on = true;
+    rc = solve_impl(sb, h->yred, (int64_t)h->gm.G * h->gm.n, d, ldd, k, b, ldb, iters, relres, s);
+    sb->c1x_on = false;
+    return rc;
   }
   const Geom& gm = h->gm;
   const int64_t m = gm.M * gm.G;
@@ -1811,6 +1838,7 @@ void glm_sur_destroy(glm_sur_t h) {
   dfree(h->wfwd); dfree(h->lam1); dfree(h->opart);
   dfree(h->ne_buf); dfree(h->ne_ibuf); dfree(h->ne_om);
   dfree(h->p3_buf); dfree(h->p3_ibuf);
+  dfree(h->c1x); dfree(h->c1x_part);
   if (h->p3_hact) cudaFreeHost(h->p3_hact);
   if (h->ne_hact) cudaFreeHost(h->ne_hact);
   if (h->h_done) cudaFreeHost(h->h_done);

@@ -420,7 +420,7 @@ __device__ void solve_instance(const BatchInst& dsc, const BatchPools& P, const 
       const int j = tid;
       const double cur = sqrt(sm.colv[j]);
       revert[j] = 0;
-      if (outer == 0) rho0[j] = cur;
+      if (outer == 0) rho0[j] = P.rho_extra ? sqrt(cur * cur + P.rho_extra[(int64_t)dsc.index * kBatchMaxK + j]) : cur;
       if (fin[j] == kStatusRunning) {
         const double rr = rho0[j] > 0 ? cur / rho0[j] : 0.0;
         if (!isfinite(cur)) fin[j] = GLM_SUR_NONFINITE;

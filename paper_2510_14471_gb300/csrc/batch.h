@@ -44,6 +44,10 @@ struct BatchPools {
   double* relres;
   int* steps;                // per instance: float32 steps the CTA ran (all refinement rounds)
   long long* cycles;         // per instance: SM clock cycles from start to end
+  // (nullable, count x kBatchMaxK) energy added to the first float64 residual as the
+  // reference of relres and tol: a row-reduced instance's share of the
+  // M-row model's ||P y||^2 that the reduction leaves out
+  const double* rho_extra;
 };
 
 struct BatchOpts {

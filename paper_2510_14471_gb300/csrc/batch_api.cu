@@ -58,6 +58,13 @@ struct glm_sur_batch_ctx {
   DgemmProblem* d_rot = nullptr;        // rotation problems of the last (Y, k)
   const double* rot_y = nullptr;
   int rot_k = 0, rot_count = 0, rot_tiles = 0;
+  // energy of every instance's responses outside range(W_j) (count x K), the
+  // reference term of the reduced instances' relres and tol; on `inner` the
+  // outer handle's buffer
+  struct RedRows { int64_t y_off, yr_off, m, mr; int red; };
+  RedRows* d_redrows = nullptr;
+  double* d_extra = nullptr;
+  const double* rho_extra = nullptr;
 };
 
 namespace {
@@ -66,6 +73,30 @@ template <typename T>
 cudaError_t balloc(T** p, size_t n) {
   *p = nullptr;
   return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+// out[j K + c] = max(0, ||y_jc||^2 - ||Q_W^T y_jc||^2) for a reduced instance
+// j (0 for the others): one CTA per (instance, right-hand side)
+__global__ void __launch_bounds__(256)
+k_batch_complement(int k, const glm_sur_batch_ctx::RedRows* __restrict__ rr, const double* __restrict__ Y,
+                   const double* __restrict__ Yr, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int j = blockIdx.x, c = blockIdx.y;
+  const glm_sur_batch_ctx::RedRows d = rr[j];
+  double a = 0.0;
+  if (d.red) {
+    const double* y = Y + d.y_off * k + (int64_t)c * d.m;
+    const double* yr = Yr + d.yr_off * k + (int64_t)c * d.mr;
+    for (int64_t t = threadIdx.x; t < d.m; t += 256) a += y[t] * y[t];
+    for (int64_t t = threadIdx.x; t < d.mr; t += 256) a -= yr[t] * yr[t];
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(int64_t)j * kBatchMaxK + c] = red[0] > 0.0 ? red[0] : 0.0;
 }
 template <typename T>
 void bfree(T*& p) {
@@ -284,6 +315,20 @@ static glm_sur_status batch_setup_reduced(glm_sur_batch_t* out, int count, const
   h->G.assign(G, G + count);
   h->M.assign(M, M + count);
   h->n = n;
+  {
+    std::vector<glm_sur_batch_ctx::RedRows> rows(count);
+    for (int j = 0; j < count; ++j)
+      rows[j] = {h->y_off[j], h->yr_off[j], (int64_t)G[j] * M[j], (int64_t)G[j] * Mr[j], h->red[j]};
+    cudaError_t e = balloc(&h->d_redrows, (size_t)count);
+    if (e == cudaSuccess) e = balloc(&h->d_extra, (size_t)count * kBatchMaxK);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_redrows, rows.data(), sizeof(glm_sur_batch_ctx::RedRows) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_last_error(e, "cudaMalloc (batch row reduction)", __FILE__, __LINE__);
+      glm_sur_batch_destroy(h);
+      return GLM_SUR_CUDA_ERROR;
+    }
+  }
   *out = h;
   return GLM_SUR_OK;
 }
@@ -462,8 +507,14 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
       if (!h->red[j])
         GS_CUDA_TRY(cudaMemcpyAsync(h->yred + h->yr_off[j] * k, Y + h->y_off[j] * k,
                                     sizeof(double) * (size_t)h->G[j] * h->M[j] * k, cudaMemcpyDeviceToDevice, s));
+    // tol and relres of every reduced instance refer to its M-row model's
+    // ||P y||: the reduced ||P' y'||^2 plus the energy of y outside range(W)
+    k_batch_complement<<<dim3((unsigned)h->count, (unsigned)k), 256, 0, s>>>(k, h->d_redrows, Y, h->yred,
+                                                                             h->d_extra);
+    h->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     h->last_k = k;
+    h->inner->rho_extra = h->d_extra;
     return glm_sur_batch_solve(h->inner, h->yred, k, b, iters, relres, stream);
   }
   if (h->maxNq * k > kBatchMaxPairs) return GLM_SUR_INVALID_ARG;
@@ -496,7 +547,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
   }
   BatchPools P{h->q64, h->q32, h->R, h->om64, h->om32, h->d_n_i, h->d_poff, h->d_r_off, h->d_quad_blk,
                h->w64, h->E64, h->d64, h->g32, h->u32, h->w32, h->wb32, Y, b, h->status, h->iters_d,
-               h->relres_d, h->steps_d, h->cycles_d};
+               h->relres_d, h->steps_d, h->cycles_d, h->rho_extra};
   BatchOpts bo{h->opts.tol, h->opts.inner_tol, h->opts.max_refine, 4000, 25};
   if (h->tile == 0) {
     // autotune: time one batch solve per tile height, tallest first, keep the
@@ -539,7 +590,7 @@ glm_sur_status glm_sur_batch_solve(glm_sur_batch_t h, const double* Y, int k, do
     GS_CUDA_TRY(write_work_order(h, k, cost));
   }
   // one persistent launch, replayed from a captured graph while the buffers stay the same
-  const void* key[5] = {Y, b, iters, relres, nullptr};
+  const void* key[5] = {Y, b, iters, relres, h->rho_extra};
   if (!h->graph || h->graph_k != k || std::memcmp(key, h->graph_key, sizeof key) != 0) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -618,6 +669,8 @@ void glm_sur_batch_destroy(glm_sur_batch_t h) {
     bfree(h->qw);
     bfree(h->yred);
     bfree(h->d_rot);
+    bfree(h->d_redrows);
+    bfree(h->d_extra);
     delete h;
     return;
   }

@@ -99,6 +99,10 @@ struct PcgState {
   int* it = nullptr;                   // completed steps (written by the reduce kernel)
   int* done = nullptr;
   int* err = nullptr;                  // set when a bounded device wait gave up
+  // (nullable, k) energy added to the first c as the reference of relres and
+  // the tolerance: a row-reduced model's share of the M-row model's
+  // ||P y||^2 that the reduction leaves out
+  const double* c1_extra = nullptr;
 };
 
 }  // namespace glmsur

@@ -69,13 +69,15 @@ __global__ void k_pcg3_after(Pcg3State st, const double* __restrict__ cpart, int
   double cn = 0.0;
   for (int p = 0; p < ncpart; ++p) cn += cpart[(int64_t)p * st.k + j];
   if (init) {
+    const double c1v = cn + (st.c1_extra ? st.c1_extra[j] : 0.0);
     st.c[j] = cn;
-    st.c1[j] = cn;
+    st.c1[j] = c1v;
     st.iters[j] = 0;
     const bool fin = isfinite(cn);
-    st.active[j] = fin && cn > 0.0;
-    st.status[j] = !fin ? (int)GLM_SUR_NONFINITE : (cn > 0.0 ? kStatusRunning : (int)GLM_SUR_OK);
-    st.relres[j] = cn > 0.0 ? 1.0 : 0.0;
+    const bool conv0 = fin && st.c1_extra != nullptr && cn <= st.tol * st.tol * c1v;
+    st.active[j] = fin && cn > 0.0 && !conv0;
+    st.status[j] = !fin ? (int)GLM_SUR_NONFINITE : ((cn > 0.0 && !conv0) ? kStatusRunning : (int)GLM_SUR_OK);
+    st.relres[j] = (fin && cn > 0.0) ? sqrt(cn / c1v) : 0.0;
     st.mu[j] = 0.0;
     return;
   }

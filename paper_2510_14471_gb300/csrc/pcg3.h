@@ -15,6 +15,7 @@ struct Pcg3State {
   int *active = nullptr, *iters = nullptr, *status = nullptr;
   double* dpart = nullptr;   // nblk x k partial sums of d
   int nblk = 0;
+  const double* c1_extra = nullptr;   // (nullable, k) added to the first c (reduced handles)
 };
 
 // Sm = -Sigma u (as the Sigma-residual kernel returns it for a zero right side).

@@ -26,20 +26,23 @@ __device__ __forceinline__ StepScalars step_prologue(const PcgState& st, int j, 
   const int it = *st.it;
   out.lam_prev = st.lam[j];
   if (it == 0) {
-    const bool act = (csum > 0.0) && isfinite(csum);
+    const double c1v = csum + (st.c1_extra ? st.c1_extra[j] : 0.0);
+    const bool fin = isfinite(csum);
+    const bool conv0 = fin && st.c1_extra != nullptr && csum <= st.tol * st.tol * c1v;   // converged at the start
+    const bool act = (csum > 0.0) && fin && !conv0;
     out.act = act;
     out.act_prev = 1;
     out.mu = 0.0;
     if (writer) {
-      st.c1[j] = csum;
+      st.c1[j] = c1v;
       st.c[0][j] = csum;
       st.active[0][j] = act;
       st.cbest[0][j] = csum;
       st.itbest[0][j] = 0;
       st.csnap[0][j] = csum;
       st.cstop[j] = csum;
-      st.relres[j] = act ? 1.0 : 0.0;
-      st.status[j] = act ? kStatusRunning : (isfinite(csum) ? GLM_SUR_OK : GLM_SUR_NONFINITE);
+      st.relres[j] = (fin && csum > 0.0) ? sqrt(csum / c1v) : 0.0;
+      st.status[j] = act ? kStatusRunning : (fin ? GLM_SUR_OK : GLM_SUR_NONFINITE);
       st.iters[j] = 0;
     }
     return out;

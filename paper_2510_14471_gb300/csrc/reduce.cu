@@ -144,4 +144,43 @@ void launch_zero_upper(int n, double* A, cudaStream_t s) {
   k_zero_upper<<<(unsigned)ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, A);
 }
 
+
+namespace {
+
+// part[j G + i] = s_i^2 (||y_ij||^2 - ||Q^T y_ij||^2): one CTA per (equation, rhs)
+__global__ void __launch_bounds__(256)
+k_complement_energy(int G, int64_t M, int64_t n, const double* __restrict__ Y, int64_t ldy,
+                    const double* __restrict__ Yr, const double* __restrict__ isq, double* __restrict__ part) {
+  __shared__ double red[256];
+  const int i = blockIdx.x, j = blockIdx.y;
+  const double* y = Y + (int64_t)j * ldy + (int64_t)i * M;
+  const double* yr = Yr + ((int64_t)j * G + i) * n;
+  double a = 0.0;
+  for (int64_t t = threadIdx.x; t < M; t += 256) a += y[t] * y[t];
+  for (int64_t t = threadIdx.x; t < n; t += 256) a -= yr[t] * yr[t];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)j * G + i] = isq ? red[0] * isq[i] * isq[i] : red[0];
+}
+
+__global__ void k_complement_sum(int G, int k, const double* __restrict__ part, double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= k) return;
+  double t = 0.0;
+  for (int i = 0; i < G; ++i) t += part[(int64_t)j * G + i];
+  out[j] = t > 0.0 ? t : 0.0;
+}
+
+}  // namespace
+
+void launch_complement_energy(int G, int64_t M, int64_t n, int k, const double* Y, int64_t ldy, const double* Yr,
+                              const double* isq, double* part, double* out, cudaStream_t s) {
+  k_complement_energy<<<dim3((unsigned)G, (unsigned)k), 256, 0, s>>>(G, M, n, Y, ldy, Yr, isq, part);
+  k_complement_sum<<<1, 64, 0, s>>>(G, k, part, out);
+}
+
 }  // namespace glmsur

@@ -35,6 +35,13 @@ void launch_dgemm_batched(const DgemmProblem* probs, int count, int max_tiles, c
 // triangle is ignored); Linv row-major with zeros above the diagonal.
 cudaError_t launch_tri_inverse(int n, const double* L, double* Linv, cudaStream_t s);
 
+// Energy of the responses outside range(W), per right-hand side j:
+// out[j] = max(0, sum_i s_i^2 (||y_ij||^2 - ||Q^T y_ij||^2)), y_ij = Y[j * ldy
+// + i M ...] (M rows), Q^T y_ij = Yr[(j G + i) n ...] (n rows), s = isq or
+// ones (the row scaling of a preconditioner block).  part: G x k workspace.
+void launch_complement_energy(int G, int64_t M, int64_t n, int k, const double* Y, int64_t ldy, const double* Yr,
+                              const double* isq, double* part, double* out, cudaStream_t s);
+
 // Zero the strict upper triangle of a row-major n x n matrix.
 void launch_zero_upper(int n, double* A, cudaStream_t s);
 
