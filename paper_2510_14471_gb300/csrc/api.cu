@@ -120,6 +120,8 @@ struct glm_sur_ctx {
   double* Qw = nullptr;        // M x n column-major orthonormal basis of range(W)
   double* yred = nullptr;      // reduced responses / gradients, (G n) x k column-major
   int64_t yred_cap = 0;
+  double* rot_ws = nullptr;    // depth-split partial products of the rotation
+  int64_t rot_ws_cap = 0;
   // (on the reduced model) energy of the responses outside range(W), k
   // values, added to the reference of relres and tol while c1x_on
   double* c1x = nullptr;
@@ -702,6 +704,8 @@ glm_sur_status setup_reduced(glm_sur_t* out, int G, int64_t M, const int* n_i, i
   h->gm.Ms = M;
   h->gm.n = n;
   h->n_i.assign(n_i, n_i + G);
+  h->dev = sub->dev;
+  h->sms = sub->sms;
   h->launches = 11;
   *out = h;
   return GLM_SUR_OK;
@@ -717,13 +721,25 @@ glm_sur_status rotate_in(glm_sur_ctx* h, const double* Y, int64_t ldy, int k, cu
     GS_CUDA_TRY(dalloc(&h->yred, (size_t)need));
     h->yred_cap = need;
   }
-  if (ldy == M * G) {
-    launch_dgemm((int)n, (int)(G * k), M, h->Qw, M, 1, Y, 1, M, h->yred, 1, n, s);
-    h->launches += 1;
+  // depth-split products when the n x G k output has too few tiles for the SMs
+  const bool one = ldy == M * G;
+  const int ncols = (int)(one ? G * k : G);
+  const int nz = dgemm_split((int)n, ncols, M, h->sms);
+  if (nz > 1 && (int64_t)nz * n * ncols > h->rot_ws_cap) {
+    dfree(h->rot_ws);
+    h->rot_ws_cap = 0;
+    GS_CUDA_TRY(dalloc(&h->rot_ws, (size_t)nz * n * ncols));
+    h->rot_ws_cap = (int64_t)nz * n * ncols;
+  }
+  double* ws = nz > 1 ? h->rot_ws : nullptr;
+  const int per = nz > 1 ? 2 : 1;
+  if (one) {
+    launch_dgemm((int)n, ncols, M, h->Qw, M, 1, Y, 1, M, h->yred, 1, n, s, ws, nz);
+    h->launches += per;
   } else {
     for (int j = 0; j < k; ++j)
-      launch_dgemm((int)n, (int)G, M, h->Qw, M, 1, Y + (int64_t)j * ldy, 1, M, h->yred + j * G * n, 1, n, s);
-    h->launches += k;
+      launch_dgemm((int)n, ncols, M, h->Qw, M, 1, Y + (int64_t)j * ldy, 1, M, h->yred + j * G * n, 1, n, s, ws, nz);
+    h->launches += per * k;
   }
   GS_CUDA_TRY(cudaGetLastError());
   return GLM_SUR_OK;
@@ -1822,6 +1838,7 @@ void glm_sur_destroy(glm_sur_t h) {
     cudaDeviceSynchronize();
     dfree(h->Qw);
     dfree(h->yred);
+    dfree(h->rot_ws);
     dfree(h->mv_koff);
     dfree(h->mv_Q0);
     dfree(h->mv_y);

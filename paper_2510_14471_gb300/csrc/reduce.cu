@@ -9,6 +9,8 @@
 // the basis are float64 data).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "reduce.h"
 
@@ -74,6 +76,29 @@ k_dgemm(int m, int n, int64_t kdim, const double* __restrict__ A, int64_t ars, i
   dgemm_tile(blockIdx.y * kTM, blockIdx.x * kTN, m, n, kdim, A, ars, acs, B, brs, bcs, C, crs, ccs);
 }
 
+// Depth-split product: CTA (x, y, z) computes tile (y, x) over depth chunk z
+// into ws[z] (m x n row-major); the chunks are summed by k_dgemm_sum.
+__global__ void __launch_bounds__(256)
+k_dgemm_split(int m, int n, int64_t kdim, int64_t kc, const double* __restrict__ A, int64_t ars, int64_t acs,
+              const double* __restrict__ B, int64_t brs, int64_t bcs, double* __restrict__ ws) {
+  const int64_t p0 = (int64_t)blockIdx.z * kc;
+  const int64_t len = kdim - p0 < kc ? kdim - p0 : kc;
+  dgemm_tile(blockIdx.y * kTM, blockIdx.x * kTN, m, n, len, A + p0 * acs, ars, acs, B + p0 * brs, brs, bcs,
+             ws + (int64_t)blockIdx.z * m * n, n, 1);
+}
+
+// C(i, j) = sum over the chunks z = 0, 1, ... of ws[z](i, j) (fixed order)
+__global__ void k_dgemm_sum(int m, int n, int nz, const double* __restrict__ ws, double* __restrict__ C, int64_t crs,
+                            int64_t ccs) {
+  const int64_t mn = (int64_t)m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int z = 0; z < nz; ++z) t += ws[z * mn + e];
+    const int64_t i = e / n, j = e - i * n;
+    C[i * crs + j * ccs] = t;
+  }
+}
+
 // grid (tiles, problems): CTA (t, q) computes tile t of problem q (row-major
 // over its tiles), or nothing when problem q has fewer tiles
 __global__ void __launch_bounds__(256) k_dgemm_batched(const DgemmProblem* __restrict__ probs) {
@@ -119,8 +144,26 @@ __global__ void k_zero_upper(int n, double* __restrict__ A) {
 
 }  // namespace
 
+int dgemm_split(int m, int n, int64_t kdim, int sms) {
+  const int64_t tiles = ceil_div(m, kTM) * ceil_div(n, kTN);
+  int64_t z = ceil_div((int64_t)16 * sms, tiles);   // about 16 CTAs per SM
+  z = std::min<int64_t>(z, 32);
+  z = std::min<int64_t>(z, kdim / 512);              // chunks of at least 512
+  return (int)std::max<int64_t>(z, 1);
+}
+
 void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int64_t acs, const double* B,
-                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s) {
+                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s, double* ws,
+                  int nz) {
+  if (ws != nullptr && nz > 1) {
+    const int64_t kc = ceil_div(ceil_div(kdim, nz), kTK) * kTK;
+    const int z = (int)ceil_div(kdim, kc);
+    k_dgemm_split<<<dim3((unsigned)ceil_div(n, kTN), (unsigned)ceil_div(m, kTM), (unsigned)z), 256, 0, s>>>(
+        m, n, kdim, kc, A, ars, acs, B, brs, bcs, ws);
+    const int64_t mn = (int64_t)m * n;
+    k_dgemm_sum<<<(unsigned)std::min<int64_t>(ceil_div(mn, 256), 152 * 8), 256, 0, s>>>(m, n, z, ws, C, crs, ccs);
+    return;
+  }
   dim3 grid((unsigned)ceil_div(n, kTN), (unsigned)ceil_div(m, kTM));
   k_dgemm<<<grid, 256, 0, s>>>(m, n, kdim, A, ars, acs, B, brs, bcs, C, crs, ccs);
 }

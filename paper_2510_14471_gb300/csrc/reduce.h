@@ -11,8 +11,14 @@ namespace glmsur {
 // C(i, j) = sum_p A(i, p) B(p, j) for i < m, j < n, p < kdim, float64, with
 // A(i, p) at A[i * ars + p * acs], B(p, j) at B[p * brs + j * bcs] and C(i, j)
 // at C[i * crs + j * ccs] (any layout: strides carry transposes).
+// With a workspace ws of nz * m * n doubles and nz > 1 the depth is split in
+// nz chunks (partial tiles into ws, then summed in a fixed order): the grid
+// then fills the SMs when m x n has few tiles and the depth is long.
 void launch_dgemm(int m, int n, int64_t kdim, const double* A, int64_t ars, int64_t acs, const double* B,
-                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s);
+                  int64_t brs, int64_t bcs, double* C, int64_t crs, int64_t ccs, cudaStream_t s,
+                  double* ws = nullptr, int nz = 1);
+// Depth chunks for launch_dgemm on `sms` SMs (1: no split).
+int dgemm_split(int m, int n, int64_t kdim, int sms);
 
 // One float64 product C = A B of a batch (layout as launch_dgemm).
 struct DgemmProblem {
