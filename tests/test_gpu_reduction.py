@@ -86,3 +86,26 @@ def test_reduced_full_size_singular_workload():
     r = solver(p, precision="fp32_refine", reduce_rows=True).solve(p.Y)
     assert all(s in (0, 4) for s in r.status), r.status
     assert relcols(r.b.cpu().numpy(), p.beta) <= TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_reduced_tolerance_refers_to_the_full_model(precision):
+    # y = X beta + e with e almost all outside range(W): ||Pi y|| of the
+    # M-row model is about 1e8 times ||Pi' y'|| of the reduced one.  A
+    # tolerance relative to ||Pi y|| (the full model's) is met at the start
+    # of the reduced solve; one relative to ||Pi' y'|| would have to iterate.
+    p = S.make_problem(G=4, M=2000, n_i=[3, 5, 2, 4], k=2, seed=604, omega="chol")
+    Q = O.range_basis(np.hstack(p.X_blocks))
+    g = S.rng(605)
+    Y = np.empty_like(p.Y)
+    for i, X in enumerate(p.X_blocks):
+        z = g.standard_normal((p.M, p.k))
+        e = z - Q @ (Q.T @ z) + 1e-8 * g.standard_normal((p.M, p.k))
+        off = sum(p.n_i[:i])
+        Y[i * p.M:(i + 1) * p.M] = X @ p.beta[off:off + X.shape[1]] + e
+    h = solver(p, precision=precision, reduce_rows=True, tol=1e-6)
+    r = h.solve(Y)
+    assert list(r.status) == [0] * p.k, r.status
+    assert int(r.iters.max()) == 0, r.iters
+    assert float(r.relres.max()) <= 1e-6
+    assert relcols(r.b.cpu().numpy(), O.sur_gls_structured(p.X_blocks, p.Omega, Y)) <= 1e-6
