@@ -197,7 +197,7 @@ def run_extras(timeout_s=420):
     out = {}
     for w in EXTRA_WORKLOADS:
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", w, "--steps", "1", "--warmup", "1",
-               "--no-cpu", "--no-reduced"]
+               "--no-cpu"]
         t0 = time.perf_counter()
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
