@@ -420,16 +420,21 @@ def test_reduced_projected_residual_plus_complement_energy_is_the_full_one():
     # outside range(W) carry no regressor, so for each equation
     # ||Pi y_i||^2 = ||Pi' y_i'||^2 + ||y_i||^2 - ||Q^T y_i||^2 (y_i' = Q^T y_i,
     # X_i' = Q^T X_i): the reference of the reduced solve's tolerance
+    # The identity holds equation by equation, so it also holds under the row
+    # scaling of a preconditioner block (equation i weighted by 1/delta_i).
     p = S.make_problem(G=4, M=300, n_i=[3, 5, 2, 4], k=3, seed=91, omega="chol")
     Q = O.range_basis(np.hstack(p.X_blocks))
-    full = red = comp = 0.0
+    delta = O.jacobi_delta(p.Omega)
+    tot = np.zeros((2, p.k))
     for i, X in enumerate(p.X_blocks):
         y = p.Y[i * p.M:(i + 1) * p.M]
         Qi = O.range_basis(X)
-        full = full + np.sum((y - Qi @ (Qi.T @ y)) ** 2, axis=0)
+        full = np.sum((y - Qi @ (Qi.T @ y)) ** 2, axis=0)
         yr, Xr = Q.T @ y, Q.T @ X
         Qri = O.range_basis(Xr)
-        red = red + np.sum((yr - Qri @ (Qri.T @ yr)) ** 2, axis=0)
-        comp = comp + np.sum(y ** 2, axis=0) - np.sum(yr ** 2, axis=0)
-    assert np.all(comp > 0.5 * full)           # most of the noise lies outside range(W)
-    assert np.max(np.abs(full - (red + comp)) / full) < 1e-12
+        red = np.sum((yr - Qri @ (Qri.T @ yr)) ** 2, axis=0)
+        comp = np.sum(y ** 2, axis=0) - np.sum(yr ** 2, axis=0)
+        assert np.all(comp > 0.5 * full)       # most of the noise lies outside range(W)
+        assert np.max(np.abs(full - (red + comp)) / full) < 1e-12
+        tot += np.vstack([full, red + comp]) / delta[i]
+    assert np.max(np.abs(tot[0] - tot[1]) / tot[0]) < 1e-12
