@@ -929,7 +929,7 @@ def run_differentiable(args, rank, world, local, pg):
                          value, "forward+adjoint/s", ms, "f64",
                          {"G": G, "M": M, "n": n, "k": 1, "precision": "fp64", "precond": "diag",
                           "reduce_rows": True, "rows_per_equation": n, "tol": 1e-13, "stagnation_window": 1000,
-                          "l2": "inputs larger than L2 (Y 41 MB, X 574 MB read by the rotation products); "
+                          "l2": "every solve reads the basis Q_W (574 MB, larger than L2) in its rotation; "
                                 "reduced factor 25.7 MB L2-resident"})
         line.update({
             "rel_err_b": err_b, "rel_err_dOmega_sampled": err_om,
